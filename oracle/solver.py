@@ -1,0 +1,175 @@
+"""Inexact Gauss-Newton-Krylov solver (Sec. 2.5.5, 2.5.6, 2.6; Algorithms 1 and 2).
+
+* pcg        Algorithm 2: matrix-free PCG for H v~ = -g with the spectral
+             regularisation preconditioner M = alpha L (Sec. 2.5.6).
+             Reading C-8: stop when ||r||_2 <= eta ||g||_2 with the superlinear
+             forcing eta = min(1/2, sqrt(||g^k||_inf / ||g^0||_inf)) (quadratic:
+             without the square root).  Negative curvature <s, H s> <= 0 ends
+             PCG with the previous iterate (Sec. 2.5.5).
+* armijo     backtracking line search (reading C-9: gamma_0 = 1, factor 1/2,
+             c1 = 1e-4, directional derivative h^3 sum g . v~, at most 10 halvings).
+* gauss_newton  Algorithm 1 with the stopping rule ||g^k||_inf <= eps_opt
+             ||g^0||_inf or ||g^k||_inf <= 1e-6 (Sec. 2.5.5); g^0 is the gradient
+             at v = 0 (reading C-10).
+* continuation  solve for a decreasing sequence of beta_v, warm-starting each
+             level from the previous one (Sec. 2.6).
+Inner products are FP64 sums over all voxels and components.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .reduced import evaluate, evaluate_objective, complete_gradient, hessian_matvec
+from .spectral import apply_reg_inverse
+
+OK, ENOTCONV, ENEGCURV, ELINESEARCH = 0, 5, 6, 7
+
+
+@dataclass
+class Options:
+    eps_opt: float = 5e-2
+    max_newton: int = 50
+    max_pcg: int = 100
+    fixed_iters: bool = False     # run exactly max_newton x max_pcg (parity runs)
+    forcing: str = "superlinear"  # or "quadratic"
+    full_newton: bool = False
+    c1: float = 1e-4
+    max_halvings: int = 10
+    gabs_tol: float = 1e-6
+
+
+@dataclass
+class Stats:
+    newton_iters: int = 0
+    pcg_iters: int = 0
+    matvecs: int = 0
+    pde_solves: int = 0
+    linesearch_halvings: int = 0
+    J0: float = 0.0
+    J: float = 0.0
+    mismatch_rel: float = 0.0
+    grad_rel: float = 0.0
+    status: int = OK
+    history: list = field(default_factory=list)
+
+
+def dot(a, b):
+    return float(np.sum(np.asarray(a, dtype=np.float64) * np.asarray(b, dtype=np.float64)))
+
+
+def pcg(apply_H, apply_Minv, g, tol, max_iter, fixed=False):
+    """Algorithm 2: PCG for H v~ = -g starting from v~ = 0.
+
+    Returns (v~, iterations, matvecs, status).  tol is the absolute 2-norm
+    threshold on the residual (the caller forms eta ||g||_2).
+    """
+    vt = np.zeros_like(g)
+    r = -g
+    z = apply_Minv(r)
+    s = z.copy()
+    rz = dot(r, z)
+    matvecs = 0
+    it = 0
+    status = OK
+    for it in range(1, max_iter + 1):
+        Hs = apply_H(s)
+        matvecs += 1
+        sHs = dot(s, Hs)
+        if sHs <= 0.0:
+            status = ENEGCURV
+            if it == 1:
+                vt = s          # no previous iterate: take the preconditioned gradient
+            it -= 1
+            break
+        kappa = rz / sHs
+        vt = vt + kappa * s
+        r = r - kappa * Hs
+        if not fixed and np.sqrt(dot(r, r)) < tol:
+            break
+        z = apply_Minv(r)
+        rz_new = dot(z, r)
+        mu = rz_new / rz
+        rz = rz_new
+        s = z + mu * s
+    return vt, it, matvecs, status
+
+
+def armijo(prob, ev, vt, opts):
+    """Backtracking on J(v + gamma v~) <= J(v) + c1 gamma h^3 <g, v~> (reading C-9)."""
+    slope = prob.h3 * dot(ev.g, vt)
+    gamma = 1.0
+    for halvings in range(opts.max_halvings + 1):
+        trial = evaluate_objective(prob, ev.v + gamma * vt)
+        if trial.J <= ev.J + opts.c1 * gamma * slope:
+            return gamma, trial, halvings, True
+        gamma *= 0.5
+    return 0.0, None, opts.max_halvings, False
+
+
+def gauss_newton(prob, v0=None, opts=None, gnorm0=None, stats=None):
+    """Algorithm 1 (outer iterations) with Algorithm 2 for each Newton step."""
+    opts = opts or Options()
+    stats = stats or Stats()
+    v = np.zeros((3,) + prob.shape) if v0 is None else np.asarray(v0, dtype=np.float64)
+    ev = evaluate(prob, v)
+    stats.pde_solves += 2
+    if gnorm0 is None:
+        if np.any(v != 0.0):
+            gnorm0 = float(np.max(np.abs(evaluate(prob, np.zeros_like(v)).g)))
+            stats.pde_solves += 2
+        else:
+            gnorm0 = float(np.max(np.abs(ev.g)))
+    if stats.newton_iters == 0 and stats.J0 == 0.0:
+        stats.J0 = ev.J
+    mis0 = 0.5 * prob.h3 * np.sum((prob.m0 - prob.m1) ** 2)
+    k = 0
+    while k < opts.max_newton:
+        gnorm = float(np.max(np.abs(ev.g)))
+        if not opts.fixed_iters and (gnorm <= opts.eps_opt * gnorm0 or gnorm <= opts.gabs_tol):
+            break
+        ratio = gnorm / gnorm0
+        eta = min(0.5, np.sqrt(ratio) if opts.forcing == "superlinear" else ratio)
+        tol = eta * np.sqrt(dot(ev.g, ev.g))
+        vt, its, mv, st = pcg(lambda s: hessian_matvec(prob, ev, s, opts.full_newton),
+                              lambda r: apply_reg_inverse(r, prob.beta_v, prob.gamma),
+                              ev.g, tol, opts.max_pcg, opts.fixed_iters)
+        stats.pcg_iters += its
+        stats.matvecs += mv
+        stats.pde_solves += 2 * mv
+        gamma, trial, halvings, ok = armijo(prob, ev, vt, opts)
+        stats.linesearch_halvings += halvings
+        stats.pde_solves += halvings + 1
+        if not ok:
+            stats.status = ELINESEARCH
+            break
+        ev = complete_gradient(prob, trial)
+        stats.pde_solves += 1
+        k += 1
+        stats.newton_iters += 1
+        stats.history.append((k, ev.J, float(np.max(np.abs(ev.g))) / gnorm0, its, gamma))
+    stats.J = ev.J
+    stats.mismatch_rel = float(ev.mismatch / mis0) if mis0 > 0 else 0.0
+    stats.grad_rel = float(np.max(np.abs(ev.g)) / gnorm0)
+    if stats.status == OK and not opts.fixed_iters and stats.grad_rel > opts.eps_opt \
+            and float(np.max(np.abs(ev.g))) > opts.gabs_tol:
+        stats.status = ENOTCONV
+    return ev.v, stats, ev
+
+
+def continuation(prob, betas, opts=None, v0=None):
+    """Parameter continuation in beta_v (Sec. 2.6), warm-started level to level."""
+    opts = opts or Options()
+    stats = Stats()
+    v = v0
+    gnorm0 = None
+    ev = None
+    for beta in betas:
+        prob.beta_v = beta
+        if gnorm0 is None:
+            # g(v = 0) has no regularisation part, so one value serves every level
+            gnorm0 = float(np.max(np.abs(evaluate(prob, np.zeros((3,) + prob.shape)).g)))
+            stats.pde_solves += 2
+        stats.status = OK
+        v, stats, ev = gauss_newton(prob, v, opts, gnorm0=gnorm0, stats=stats)
+    return v, stats, ev
