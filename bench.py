@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the 256^3 registration hot path on one B300 (or N replicas).
+
+One step = one complete registration of the 256^3 brain-like phantom pair:
+beta_v continuation 1e-1 -> 1e-2 -> 1e-3 -> 1e-4 (Sec. 2.6), each level solved
+by inexact Gauss-Newton-Krylov to a relative gradient of 5e-2, nt = 4,
+H1-seminorm regularisation, FP32.  Inputs (m0, m1, v = 0) are resident in HBM
+when the timed region starts; the working set (~4 GB) is far larger than L2.
+
+Printed (rank 0, one JSON line): solve seconds per registration (value), plus
+Hessian matvecs/s at 256^3, the interpolation + FD8 share of HBM peak, the
+roofline of the dominant kernel (event-timed inside the timed solves), the
+end-to-end number through the host-buffer C entry point, clocks sampled
+during the timed region, and the FP64 CPU oracle as a bounded sample.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+With N > 1 (torchrun) every rank registers its own pair: replicas only, no
+collective on the data path (weak scaling).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "256³ solve s to rel-grad 5e-2; Hessian matvecs/s; interp+FD % of HBM peak"
+BETAS = [1e-1, 1e-2, 1e-3, 1e-4]
+NT = 4
+EPS_OPT = 5e-2
+MAX_PCG = 200
+SEED = 2
+CPU_SAMPLE_N = 32          # oracle sample: the workload restricted to 32^3
+INTERP_FD = ("trace", "sl_step", "adjoint_factor", "grad8", "div8", "sdot_hist", "accum_hist")
+# DRAM traffic per voxel and launch measured by ncu for the kernels below (see
+# profiles/); None when the kernel changed after the capture.
+NCU_TRAFFIC_PER_VOXEL = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="claire", choices=["claire", "reference"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--matvecs", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"claire_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n):
+    from paper_2401_17493_b300 import synth
+    m0, m1, _ = synth.ellipsoid_pair((n, n, n), seed=SEED)
+    return m0, m1
+
+
+def cpu_oracle_sample(m0, m1, n_full):
+    """FP64 oracle continuation solve of the workload restricted to 32^3, scaled by
+    the voxel ratio to the full grid (the 256^3 solve takes more iterations, so the
+    scaled figure underestimates the CPU time)."""
+    import numpy as np
+    from oracle import reduced, solver, spectral
+    ns = CPU_SAMPLE_N
+    a = spectral.restrict(m0.astype(np.float64), (ns,) * 3)
+    b = spectral.restrict(m1.astype(np.float64), (ns,) * 3)
+    t0 = time.perf_counter()
+    prob = reduced.Problem(a, b, nt=NT, beta_v=BETAS[0])
+    _, st, _ = solver.continuation(prob, BETAS, solver.Options(eps_opt=EPS_OPT, max_pcg=MAX_PCG))
+    dt = time.perf_counter() - t0
+    scale = (n_full / ns) ** 3
+    return dt * scale, dt, st
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    n = args.size
+    m0, m1 = workload(n)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(m0, m1, n)
+    vals, raw = [], []
+    for _ in range(args.steps):
+        v, dt, st = cpu_oracle_sample(m0, m1, n)
+        vals.append(v)
+        raw.append(dt)
+    value = float(np.mean(vals))
+    cores = os.cpu_count()
+    sample = (f"oracle FP64 continuation solve of the {CPU_SAMPLE_N}^3 spectral restriction of "
+              f"the {n}^3 pair ({np.mean(raw):.2f} s per solve), scaled x{(n // CPU_SAMPLE_N) ** 3}"
+              " by voxel count")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{n}^3 ellipsoid phantom pair, continuation 1e-1..1e-4, nt 4",
+                   "sample": f"{CPU_SAMPLE_N}^3"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_claire(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2401_17493_b300 import build, claire
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    n = args.size
+    shape = (n, n, n)
+    m0, m1 = workload(n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    m0d, m1d = dev(m0), dev(m1)
+    ctx = claire.Context(shape, nt=NT, beta_v=BETAS[0], eps_opt=EPS_OPT, max_newton=50,
+                         max_pcg=MAX_PCG)
+    ctx.set_images(m0d, m1d)
+    stream = torch.cuda.current_stream()
+    v = torch.zeros((3,) + shape, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        v.zero_()
+        ctx.solve_continuation(BETAS, v)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ctx.profile_reset(timing=True)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        v.zero_()
+        _, st = ctx.solve_continuation(BETAS, v)
+        stats.append(st.as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    t_max = ms_total
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    s_per_solve = t_max / 1e3 / (args.steps * world)
+    launches_per_step = sum(p["launches"] for k, p in prof.items() if k != "cufft") / args.steps
+
+    # Hessian matvecs/s at the converged point (50 back-to-back GN matvecs)
+    J, _ = ctx.objective_gradient(v, want_gradient=False)
+    vt = torch.randn((3,) + shape, device="cuda") * 1e-2
+    out = torch.empty_like(vt)
+    for _ in range(5):
+        ctx.hessian_matvec(vt, out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.matvecs):
+        ctx.hessian_matvec(vt, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    matvecs_per_s = args.matvecs / (e0.elapsed_time(e1) / 1e3)
+
+    # end to end through the host-buffer entry point: H2D m0, m1, v; solve; D2H v
+    m0h = torch.from_numpy(m0).pin_memory()
+    m1h = torch.from_numpy(m1).pin_memory()
+    vh = torch.zeros((3,) + shape).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        vh.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_host(m0h, m1h, vh, BETAS)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item()) / world
+
+    peak, peak_src = peaks()
+    mine = {k: p for k, p in prof.items() if k != "cufft" and p["timed"] > 0}
+    dom = max(mine, key=lambda k: mine[k]["ms"])
+    d = mine[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC_PER_VOXEL.get(dom)
+    interp_bytes = sum(mine[k]["bytes"] for k in INTERP_FD if k in mine)
+    interp_ms = sum(mine[k]["ms"] for k in INTERP_FD if k in mine)
+    interp_gbs = interp_bytes / (interp_ms * 1e-3) / 1e9
+    total_kernel_ms = sum(p["ms"] for p in prof.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, raw, _ = cpu_oracle_sample(m0, m1, n)
+        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle FP64 continuation solve of the {CPU_SAMPLE_N}^3 restriction "
+                         f"({raw:.2f} s), scaled x{(n // CPU_SAMPLE_N) ** 3} by voxel count"}
+
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": s_per_solve, "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{n}^3 ellipsoid phantom pair (seed {SEED}), beta_v continuation "
+                               "1e-1..1e-4, rel-grad 5e-2 per level, nt 4, H1 seminorm, FP32",
+                   "l2": "working set ~%.1f GB > 126 MB L2" % (ctx.workspace_bytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "matvecs_per_s": matvecs_per_s,
+        "interp_fd_hbm_frac": interp_gbs / peak,
+        "interp_fd_gbs": interp_gbs,
+        "solve": {"newton_iters": st0["newton_iters"], "pcg_iters": st0["pcg_iters"],
+                  "matvecs": st0["matvecs"], "pde_solves": st0["pde_solves"],
+                  "grad_rel": st0["grad_rel"], "mismatch_rel": st0["mismatch_rel"],
+                  "status": st0["status"]},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None if traffic is None else traffic * n ** 3,
+                     "peak_source": peak_src,
+                     "share_of_kernel_time": d["ms"] / total_kernel_ms},
+        "kernels": {k: {"launches": p["launches"], "ms": round(p["ms"], 3),
+                        "gbs": (p["bytes"] / (p["ms"] * 1e-3) / 1e9) if p["ms"] > 0 else None}
+                    for k, p in prof.items() if p["launches"] > 0},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(4 * n ** 3 * 5),
+                "d2h_bytes_per_step": int(4 * n ** 3 * 3)},
+        "gpu_launches": int(round(launches_per_step)),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_claire(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

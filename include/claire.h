@@ -1,0 +1,185 @@
+/*
+ * claire.h -- C ABI of a B300 (sm_103a) implementation of the hot path of
+ * CLAIRE's diffeomorphic image registration (arXiv 2401.17493): the RK2
+ * semi-Lagrangian transport solves inside an inexact Gauss-Newton-Krylov
+ * optimiser for a stationary velocity v, composed into the reduced gradient
+ * and the Hessian matvec.
+ *
+ * Conventions (every entry point):
+ *  - Grids are periodic, nx x ny x nz nodes on [-pi, pi)^3, spacing
+ *    h_i = 2 pi / n_i, node x_l = l h along increasing index (Sec. 2.5.1).
+ *  - Scalar fields are float32 arrays [nx][ny][nz], nz fastest.  Vector
+ *    fields are SoA float32 [3][nx][ny][nz].
+ *  - Pointer arguments are CALLER-OWNED DEVICE pointers unless the name ends
+ *    in _host.  The library never frees them and never keeps them past the
+ *    call (claire_set_images copies the images).
+ *  - The context owns all workspace (histories, departure points, FFT plans,
+ *    reduction scratch); it is allocated in claire_create.
+ *  - Calls are synchronous with respect to the stream given in the options
+ *    (default: the legacy default stream) and return a claire_status.  They
+ *    never abort, exit or trap; claire_last_error() gives a message.
+ *  - A context is not thread-safe; separate contexts are independent.
+ */
+#ifndef CLAIRE_H
+#define CLAIRE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct claire_ctx claire_ctx;
+
+typedef enum {
+  CLAIRE_OK = 0,
+  CLAIRE_EINVAL = 1,       /* bad argument: shape, nt, null pointer, option range   */
+  CLAIRE_ENOMEM = 2,       /* device allocation failed                              */
+  CLAIRE_ECUDA = 3,        /* a CUDA / cuFFT call failed                            */
+  CLAIRE_ENONFINITE = 4,   /* NaN or Inf met in J, g or a PCG scalar                */
+  CLAIRE_ENOTCONV = 5,     /* max_newton reached before the gradient tolerance      */
+  CLAIRE_ENEGCURV = 6,     /* PCG met <s, H s> <= 0 (previous iterate kept)         */
+  CLAIRE_ELINESEARCH = 7,  /* Armijo failed after max halvings                      */
+  CLAIRE_ETIMEOUT = 8,     /* a bounded device wait ran out                         */
+  CLAIRE_EORDER = 9        /* hessian_matvec before any objective_gradient          */
+} claire_status;
+
+typedef struct {
+  int precision;        /* 0: FP32 storage (default). 1: mixed (16-bit field storage,
+                           FP32 math and coordinates, FP64 reductions)               */
+  int hessian;          /* 0: Gauss-Newton (default, Sec. 2.5.5). 1: full Newton     */
+  double beta_w;        /* divergence-penalty weight of the near-incompressible model
+                           (Appendix); 0 = plain H1 seminorm (default)             */
+  double eps_opt;       /* relative gradient tolerance, default 5e-2 (Sec. 2.6)      */
+  int max_newton;       /* outer iteration cap, default 50                           */
+  int max_pcg;          /* PCG iteration cap per Newton step, default 100            */
+  int fixed_iters;      /* 1: run exactly max_newton x max_pcg iterations (parity)   */
+  int forcing;          /* 0: superlinear eta = min(1/2, sqrt(rel g)), 1: quadratic  */
+  void* stream;         /* cudaStream_t to run on; NULL = legacy default stream      */
+  int verbose;          /* 1: one line per Newton iteration on stderr                */
+  double gnorm0;        /* > 0: denominator of the relative gradient; <= 0: use
+                           ||g(v = 0)||_inf computed by the solver (reading C-10)    */
+} claire_options;
+
+typedef struct {
+  int newton_iters, pcg_iters, matvecs, pde_solves, linesearch_halvings;
+  double J0, J, mismatch_rel, grad_rel, gnorm0;
+  double detF_min, detF_max, detF_mean;
+  double seconds;       /* device time of the call (CUDA events)                    */
+  int status;
+} claire_stats;
+
+/* Fill *opt with the defaults listed above.  EINVAL on NULL. */
+claire_status claire_default_options(claire_options* opt);
+
+/* Create a context for an nx x ny x nz grid with nt time steps, regularisation
+ * weight beta_v (alpha in Sec. 2.2) and operator exponent gamma
+ * (L = (-Laplacian)^gamma, gamma = 1: H1 seminorm).  Sizes must be even and
+ * >= 16, nt >= 1, beta_v > 0, gamma > 0, else EINVAL.  Allocates the whole
+ * workspace (ENOMEM / ECUDA on failure, *out left NULL). */
+claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, double gamma,
+                            claire_ctx** out);
+claire_status claire_set_options(claire_ctx* ctx, const claire_options* opt);
+claire_status claire_get_options(const claire_ctx* ctx, claire_options* opt);
+/* Change beta_v (continuation, Sec. 2.6).  Invalidates the stored evaluation. */
+claire_status claire_set_beta(claire_ctx* ctx, double beta_v);
+/* Bytes of device memory the context holds (workspace high-water mark). */
+size_t claire_workspace_bytes(const claire_ctx* ctx);
+
+/* Copy template m0 and reference m1 (device, [nx][ny][nz]) into the context. */
+claire_status claire_set_images(claire_ctx* ctx, const float* m0, const float* m1);
+
+/* m(1) of the state equation (eq. transport, Sec. 2.2) for velocity v:
+ * RK2 departure points (Sec. 2.5.2) and nt homogeneous SL steps. */
+claire_status claire_transport(claire_ctx* ctx, const float* v, float* m1_out);
+
+/* Objective J (eq. varopt-claire) and reduced gradient g (eq. rgrad, plus the
+ * near-incompressible projection when beta_w > 0) at v.  J is a host double;
+ * g may be NULL.  Stores the state for claire_hessian_matvec. */
+claire_status claire_objective_gradient(claire_ctx* ctx, const float* v, double* J_host,
+                                        float* g);
+
+/* H vt (eq. matvec; Gauss-Newton unless options.hessian = 1) at the v of the
+ * last claire_objective_gradient / claire_solve.  EORDER if there is none. */
+claire_status claire_hessian_matvec(claire_ctx* ctx, const float* vt, float* Hvt);
+
+/* Inexact Gauss-Newton-Krylov solve (Algorithms 1 and 2) from the initial
+ * guess in v_inout; the result overwrites it.  stats may be NULL.  Returns
+ * OK, ENOTCONV, ELINESEARCH or ENONFINITE (v_inout then holds the last
+ * accepted iterate), or an argument/CUDA error. */
+claire_status claire_solve(claire_ctx* ctx, float* v_inout, claire_stats* stats);
+
+/* Parameter continuation (Sec. 2.6): solve for betas[0], betas[1], ... in
+ * turn, each level warm-started from the previous one; the relative-gradient
+ * denominator is ||g(v = 0)||_inf for every level (g(0) has no regularisation
+ * term).  The context's beta_v ends at betas[nlevels - 1].  stats accumulate
+ * over the levels. */
+claire_status claire_solve_continuation(claire_ctx* ctx, const double* betas, int nlevels,
+                                        float* v_inout, claire_stats* stats);
+
+/* claire_solve / claire_solve_continuation with HOST buffers: copies m0, m1
+ * and the initial v in, solves (betas == NULL: one level at the context's
+ * beta_v; else nlevels continuation levels), copies v out, all on the
+ * context's stream.  Pageable or pinned host memory ([nx][ny][nz] images,
+ * [3][nx][ny][nz] v).  The images replace those of claire_set_images. */
+claire_status claire_solve_host(claire_ctx* ctx, const float* m0_host, const float* m1_host,
+                                const double* betas, int nlevels, float* v_inout_host,
+                                claire_stats* stats);
+
+claire_status claire_destroy(claire_ctx* ctx);
+const char* claire_last_error(const claire_ctx* ctx);
+
+/* ---- single steps of the path (for step-by-step parity checks) ---------- */
+
+/* RK2 departure points (Sec. 2.5.2) of v as displacements in grid units:
+ * d_fwd = (y - x) / h for transport along +v (state, incremental state),
+ * d_bwd for transport along -v (adjoint, incremental adjoint).  [3][N] each;
+ * either output may be NULL. */
+claire_status claire_trace(claire_ctx* ctx, const float* v, float* d_fwd, float* d_bwd);
+
+/* out(x) = u(x + d(x)) by periodic tricubic Lagrange interpolation
+ * (Sec. 2.5.4); d is a displacement in grid units [3][N]. */
+claire_status claire_interp(claire_ctx* ctx, const float* u, const float* d, float* out);
+
+/* FD8 gradient [N] -> [3][N] and divergence [3][N] -> [N] (Sec. 2.5.3). */
+claire_status claire_grad8(claire_ctx* ctx, const float* u, float* grad_u);
+claire_status claire_div8(claire_ctx* ctx, const float* w, float* div_w);
+
+/* Spectral operators on a vector field [3][N] (Sec. 2.5.3, 2.5.6, Appendix):
+ * op 0: L = (-Laplacian)^gamma;  1: (beta_v L)^-1 with the zero symbol set to
+ * one;  2: P_par (gradient part of the Leray decomposition);  3: c(kappa) P_par
+ * (near-incompressible term with options.beta_w). */
+enum { CLAIRE_OP_L = 0, CLAIRE_OP_REG_INV = 1, CLAIRE_OP_LERAY_PAR = 2, CLAIRE_OP_NEAR_INC = 3 };
+claire_status claire_spectral(claire_ctx* ctx, int op, const float* in, float* out);
+
+/* det F1 of the deformation-gradient transport (Appendix, eq. def-grad) for
+ * velocity v: min / max / mean into minmaxmean_host[3]; det_out ([N]) may be NULL. */
+claire_status claire_det_deformation_gradient(claire_ctx* ctx, const float* v,
+                                              double* minmaxmean_host, float* det_out);
+
+/* ---- launch accounting ---------------------------------------------------
+ * The context counts every kernel it launches by class, with the algorithmic
+ * bytes each launch moves (each input field read once, each output written
+ * once; "cufft" counts one read and one write per transform).  With timing
+ * on, each launch is also bracketed by CUDA events on its stream. */
+typedef struct {
+  const char* name;     /* kernel class: trace, sl_step, adjoint_factor, grad8, div8,
+                           sdot_hist, accum_hist, spectral_diag, reduce, vector, detf, cufft */
+  long long launches;   /* launches since the last reset                              */
+  long long timed;      /* launches with an event-timed duration                     */
+  double bytes;         /* algorithmic bytes of those launches                       */
+  double ms;            /* summed event-timed duration                               */
+} claire_kernel_stat;
+
+/* Zero the counters; timing != 0 turns per-launch event timing on. */
+claire_status claire_profile_reset(claire_ctx* ctx, int timing);
+/* Waits for outstanding timing events, writes up to max entries (one per
+ * kernel class) and returns how many; with out == NULL returns the number of
+ * classes.  -1 on a NULL context or a CUDA error. */
+int claire_profile_read(claire_ctx* ctx, claire_kernel_stat* out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLAIRE_H */

@@ -1,0 +1,803 @@
+// Context, reduced-space operators, PCG / Armijo / Gauss-Newton driver and
+// the extern "C" entry points declared in include/claire.h.
+//
+// The host code only sequences kernels and reads FP64 scalars back (J, dot
+// products, norms); every field operation runs in the kernels of kernels.cu
+// and in cuFFT.  One context = one grid, one stream, one fixed workspace.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/claire.h"
+#include "internal.h"
+
+using namespace claire;
+
+struct claire_ctx {
+  Grid g{};
+  int nt = 4;
+  double beta_v = 1e-2, gamma = 1.0;
+  claire_options opt{};
+  cudaStream_t st = nullptr;
+  cufftHandle r2c = 0, c2r = 0;
+  bool plans = false;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // images and the evaluation point
+  float *m0 = nullptr, *m1 = nullptr, *v = nullptr, *df = nullptr, *db = nullptr;
+  float *D = nullptr, *cf = nullptr, *mhist = nullptr, *lhist = nullptr, *grad = nullptr;
+  float *Lv = nullptr, *scr3 = nullptr;
+  // matvec and PCG workspace
+  float *shist = nullptr, *pp0 = nullptr, *pp1 = nullptr, *lthist = nullptr;
+  float *vt = nullptr, *r = nullptr, *z = nullptr, *s = nullptr, *Hs = nullptr;
+  float *vtrial = nullptr, *dtrial = nullptr;
+  cufftComplex* cbuf = nullptr;
+  double *partial = nullptr, *dres = nullptr, *hres = nullptr;
+  int red_blocks = 1184;
+  // det F workspace (allocated on first use)
+  float* detf = nullptr;
+  bool have_eval = false;
+  double J = 0.0, dist = 0.0;
+  std::string err;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Profiler prof;
+};
+
+namespace {
+
+claire_status fail(claire_ctx* c, claire_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                           \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(ctx, CLAIRE_ECUDA, "%s failed: %s (%s:%d)", #call,                  \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+  } while (0)
+
+#define CUFFT_TRY(ctx, call)                                                          \
+  do {                                                                                \
+    cufftResult r_ = (call);                                                          \
+    if (r_ != CUFFT_SUCCESS)                                                          \
+      return fail(ctx, CLAIRE_ECUDA, "%s failed: cufft error %d", #call, (int)r_);    \
+  } while (0)
+
+#define TRY(expr)                                  \
+  do {                                             \
+    claire_status s_ = (expr);                     \
+    if (s_ != CLAIRE_OK) return s_;                \
+  } while (0)
+
+// Launch errors surface here (asynchronous faults at the next sync).
+claire_status check_launch(claire_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(c, CLAIRE_ECUDA, "kernel launch (%s) failed: %s", what, cudaGetErrorString(e));
+  return CLAIRE_OK;
+}
+
+claire_status alloc(claire_ctx* c, float** p, int64_t nfloats) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)nfloats * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CLAIRE_ENOMEM, "cudaMalloc of %lld floats failed: %s", (long long)nfloats,
+                cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  c->bytes += (size_t)nfloats * sizeof(float);
+  *p = (float*)q;
+  return CLAIRE_OK;
+}
+
+int64_t N_of(const claire_ctx* c) { return c->g.N; }
+
+// Routes the launch accounting of the kernels to this context for one API call.
+struct Enter {
+  Profiler* prev;
+  explicit Enter(claire_ctx* c) : prev(tl_prof) { tl_prof = c ? &c->prof : nullptr; }
+  ~Enter() { tl_prof = prev; }
+};
+#define ENTER(c) Enter enter_guard_(c)
+
+// ---------------------------------------------------------------- reductions
+
+claire_status reduce(claire_ctx* c, int64_t n, const float* a, const float* b, int mode,
+                     double* out) {
+  launch_reduce(n, a, b, mode, c->partial, c->red_blocks, c->dres, c->st);
+  TRY(check_launch(c, "reduce"));
+  CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  *out = c->hres[0];
+  return CLAIRE_OK;
+}
+
+claire_status dot3(claire_ctx* c, const float* a, const float* b, double* out) {
+  return reduce(c, 3 * N_of(c), a, b, RED_DOT, out);
+}
+
+// ---------------------------------------------------------------- spectral
+
+// out = op(in) for a vector field; accumulate: out = out_coef * out + op(in) via scr3.
+claire_status spectral(claire_ctx* c, int op, const float* in, float* out, double alpha) {
+  const double fft_bytes = 3.0 * (4.0 * c->g.N + 8.0 * c->g.n1 * c->g.n2 * (c->g.n3 / 2 + 1));
+  {
+    ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)in, c->cbuf));
+  }
+  launch_spectral(c->g, c->cbuf, op, (float)alpha, (float)c->gamma, (float)c->opt.beta_w, c->st);
+  TRY(check_launch(c, "spectral"));
+  {
+    ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    CUFFT_TRY(c, cufftExecC2R(c->c2r, c->cbuf, (cufftReal*)out));
+  }
+  return CLAIRE_OK;
+}
+
+// b <- b - c(kappa) P_par b when beta_w > 0 (near-incompressible model, Appendix).
+claire_status project_data_term(claire_ctx* c, float* b) {
+  if (c->opt.beta_w <= 0.0) return CLAIRE_OK;
+  TRY(spectral(c, CLAIRE_OP_NEAR_INC, b, c->scr3, c->beta_v));
+  launch_axpby(3 * N_of(c), -1.0f, c->scr3, 1.0f, b, c->st);
+  return check_launch(c, "axpby");
+}
+
+// ---------------------------------------------------------------- PDE solves
+
+float ht_of(const claire_ctx* c) { return 1.0f / (float)c->nt; }
+
+// m^0 = m0, m^{j+1}(x) = m^j(x + d_f(x))  (eq. transport, homogeneous SL steps)
+claire_status state_solve(claire_ctx* c, const float* d) {
+  const int64_t N = N_of(c);
+  CUDA_TRY(c, cudaMemcpyAsync(c->mhist, c->m0, N * sizeof(float), cudaMemcpyDeviceToDevice,
+                              c->st));
+  for (int j = 0; j < c->nt; ++j)
+    launch_sl(c->g, c->mhist + j * N, d, nullptr, 1.0f, nullptr, 0.0f, c->mhist + (j + 1) * N,
+              c->st);
+  return check_launch(c, "state_solve");
+}
+
+// J = 1/2 h^3 sum (m(1) - m1)^2 + beta_v/2 h^3 <v, L v>  (eq. varopt-claire); keeps L v.
+claire_status objective(claire_ctx* c, const float* v, double* J) {
+  const int64_t N = N_of(c);
+  const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
+  double sq = 0.0, vLv = 0.0;
+  TRY(reduce(c, N, c->mhist + c->nt * N, c->m1, RED_SQDIFF, &sq));
+  TRY(spectral(c, CLAIRE_OP_L, v, c->Lv, 1.0));
+  TRY(dot3(c, v, c->Lv, &vLv));
+  c->dist = 0.5 * h3 * sq;
+  *J = c->dist + 0.5 * c->beta_v * h3 * vLv;
+  if (!std::isfinite(*J)) return fail(c, CLAIRE_ENONFINITE, "objective is not finite (%g)", *J);
+  return CLAIRE_OK;
+}
+
+// Adjoint solve (eq. adjoint) backward from lam(1) = m1 - m(1), then
+// g = beta_v L v + [I - c P_par] sum_j w_j lam^j grad m^j  (eq. rgrad).
+claire_status adjoint_and_gradient(claire_ctx* c) {
+  const int64_t N = N_of(c);
+  const Grid& g = c->g;
+  launch_trace(g, c->v, nullptr, c->db, ht_of(c), c->st);
+  launch_div8(g, c->v, c->D, c->st);
+  launch_adjoint_factor(g, c->D, c->db, ht_of(c), c->cf, c->st);
+  launch_lincomb(N, 1.0f, c->m1, -1.0f, c->mhist + c->nt * N, c->lhist + c->nt * N, c->st);
+  for (int j = c->nt - 1; j >= 0; --j)
+    launch_sl(g, c->lhist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lhist + j * N,
+              c->st);
+  TRY(check_launch(c, "adjoint"));
+  if (c->opt.beta_w > 0.0) {
+    launch_accum_hist(g, c->lhist, c->mhist, c->nt, nullptr, 0.0f, c->grad, c->st);
+    TRY(project_data_term(c, c->grad));
+    launch_axpby(3 * N, (float)c->beta_v, c->Lv, 1.0f, c->grad, c->st);
+  } else {
+    launch_accum_hist(g, c->lhist, c->mhist, c->nt, c->Lv, (float)c->beta_v, c->grad, c->st);
+  }
+  return check_launch(c, "gradient");
+}
+
+// Full evaluation at c->v: trace, state, J, adjoint, g (Algorithm 1, lines 3-6).
+claire_status evaluate(claire_ctx* c) {
+  c->have_eval = false;
+  launch_trace(c->g, c->v, c->df, nullptr, ht_of(c), c->st);
+  TRY(check_launch(c, "trace"));
+  TRY(state_solve(c, c->df));
+  TRY(objective(c, c->v, &c->J));
+  TRY(adjoint_and_gradient(c));
+  c->have_eval = true;
+  return CLAIRE_OK;
+}
+
+// Gauss-Newton H vt (eq. matvec with the lam terms dropped):
+//  incremental state along +v with w^j = m~^j - (h_t/2) s^j, s^j = grad m^j . vt:
+//    w^0 = -(h_t/2) s^0;  w^{j+1} = w^j(y_f) - h_t s^{j+1};  m~(1) = w^{nt-1}(y_f) - (h_t/2) s^nt
+//  incremental adjoint from lam~(1) = -m~(1): lam~^j = c(x) lam~^{j+1}(y_b)
+//  H vt = beta_v L vt + [I - c P_par] sum_j w_j lam~^j grad m^j.
+claire_status matvec(claire_ctx* c, const float* vt, float* Hvt) {
+  if (!c->have_eval)
+    return fail(c, CLAIRE_EORDER, "hessian_matvec needs a prior objective_gradient");
+  const int64_t N = N_of(c);
+  const Grid& g = c->g;
+  const float ht = ht_of(c);
+  const int nt = c->nt;
+  launch_sdot_hist(g, c->mhist, nt, vt, -0.5f * ht, c->shist, c->st);
+  const float* src = c->shist;                       // w^0
+  for (int j = 0; j < nt; ++j) {
+    if (j < nt - 1) {
+      float* dst = (j % 2 == 0) ? c->pp0 : c->pp1;
+      launch_sl(g, src, c->df, nullptr, 1.0f, c->shist + (j + 1) * N, -ht, dst, c->st);
+      src = dst;
+    } else {                                         // lam~(1) = -m~(1)
+      launch_sl(g, src, c->df, nullptr, -1.0f, c->shist + nt * N, 0.5f * ht,
+                c->lthist + nt * N, c->st);
+    }
+  }
+  for (int j = nt - 1; j >= 0; --j)
+    launch_sl(g, c->lthist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lthist + j * N,
+              c->st);
+  TRY(check_launch(c, "matvec transport"));
+  TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
+  if (c->opt.beta_w > 0.0) {
+    launch_accum_hist(g, c->lthist, c->mhist, nt, nullptr, 0.0f, Hvt, c->st);
+    TRY(project_data_term(c, Hvt));
+    TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
+    launch_axpby(3 * N, (float)c->beta_v, c->scr3, 1.0f, Hvt, c->st);
+  } else {
+    launch_accum_hist(g, c->lthist, c->mhist, nt, c->scr3, (float)c->beta_v, Hvt, c->st);
+  }
+  return check_launch(c, "matvec accumulate");
+}
+
+// ---------------------------------------------------------------- Krylov / Newton
+
+struct Counters {
+  int pcg = 0, matvecs = 0, pde = 0, halvings = 0;
+};
+
+// Algorithm 2: PCG for H vt = -g from vt = 0 with M = beta_v L (zero symbol -> 1).
+claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
+  const int64_t n3 = 3 * N_of(c);
+  *curv = CLAIRE_OK;
+  CUDA_TRY(c, cudaMemsetAsync(c->vt, 0, n3 * sizeof(float), c->st));
+  launch_lincomb(n3, -1.0f, c->grad, 0.0f, c->grad, c->r, c->st);    // r = -g
+  TRY(spectral(c, CLAIRE_OP_REG_INV, c->r, c->z, c->beta_v));
+  CUDA_TRY(c, cudaMemcpyAsync(c->s, c->z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+  double rz = 0.0;
+  TRY(dot3(c, c->r, c->z, &rz));
+  for (int it = 1; it <= c->opt.max_pcg; ++it) {
+    TRY(matvec(c, c->s, c->Hs));
+    ++k.matvecs;
+    k.pde += 2;
+    double sHs = 0.0;
+    TRY(dot3(c, c->s, c->Hs, &sHs));
+    if (!std::isfinite(sHs) || !std::isfinite(rz))
+      return fail(c, CLAIRE_ENONFINITE, "PCG scalar not finite");
+    if (sHs <= 0.0) {                                 // negative curvature (Sec. 2.5.5)
+      *curv = CLAIRE_ENEGCURV;
+      if (it == 1)
+        CUDA_TRY(c, cudaMemcpyAsync(c->vt, c->s, n3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    c->st));
+      return CLAIRE_OK;
+    }
+    const double kappa = rz / sHs;
+    launch_axpby(n3, (float)kappa, c->s, 1.0f, c->vt, c->st);
+    launch_axpby(n3, (float)-kappa, c->Hs, 1.0f, c->r, c->st);
+    ++k.pcg;
+    if (!c->opt.fixed_iters) {
+      double rr = 0.0;
+      TRY(reduce(c, n3, c->r, nullptr, RED_SQ, &rr));
+      if (std::sqrt(rr) < tol) break;
+    }
+    if (it == c->opt.max_pcg) break;
+    TRY(spectral(c, CLAIRE_OP_REG_INV, c->r, c->z, c->beta_v));
+    double rz_new = 0.0;
+    TRY(dot3(c, c->z, c->r, &rz_new));
+    const double mu = rz_new / rz;
+    rz = rz_new;
+    launch_axpby(n3, 1.0f, c->z, (float)mu, c->s, c->st);           // s = z + mu s
+    TRY(check_launch(c, "pcg"));
+  }
+  return check_launch(c, "pcg");
+}
+
+// Armijo backtracking (reading C-9) on J(v + gamma vt); on success the state
+// history, departure points and L v belong to the accepted point.
+claire_status armijo(claire_ctx* c, Counters& k, double* gamma_out, bool* ok) {
+  const int64_t n3 = 3 * N_of(c);
+  const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
+  double gv = 0.0;
+  TRY(dot3(c, c->grad, c->vt, &gv));
+  const double slope = h3 * gv;
+  const double J0 = c->J;
+  double gamma = 1.0;
+  *ok = false;
+  c->have_eval = false;
+  for (int h = 0; h <= 10; ++h) {
+    launch_lincomb(n3, 1.0f, c->v, (float)gamma, c->vt, c->vtrial, c->st);
+    launch_trace(c->g, c->vtrial, c->dtrial, nullptr, ht_of(c), c->st);
+    TRY(check_launch(c, "armijo trace"));
+    TRY(state_solve(c, c->dtrial));
+    ++k.pde;
+    double Jt = 0.0;
+    claire_status s = objective(c, c->vtrial, &Jt);
+    if (s != CLAIRE_OK && s != CLAIRE_ENONFINITE) return s;
+    if (s == CLAIRE_OK && Jt <= J0 + 1e-4 * gamma * slope) {
+      std::swap(c->v, c->vtrial);
+      std::swap(c->df, c->dtrial);
+      c->J = Jt;
+      *gamma_out = gamma;
+      *ok = true;
+      k.halvings += h;
+      return CLAIRE_OK;
+    }
+    gamma *= 0.5;
+  }
+  k.halvings += 10;
+  return CLAIRE_OK;
+}
+
+claire_status absmax3(claire_ctx* c, const float* a, double* out) {
+  return reduce(c, 3 * N_of(c), a, nullptr, RED_ABSMAX, out);
+}
+
+// Algorithm 1 from the iterate in c->v; gnorm0 > 0 fixes the relative-gradient
+// denominator (reading C-10), else ||g(v = 0)||_inf is computed first.
+claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_stats* out) {
+  const int64_t n3 = 3 * N_of(c);
+  double vmax = 0.0;
+  TRY(absmax3(c, c->v, &vmax));
+  if (gnorm0 <= 0.0 && vmax > 0.0) {
+    // g(v = 0) has no regularisation term: evaluate at zero once for the denominator
+    CUDA_TRY(c, cudaMemcpyAsync(c->vtrial, c->v, n3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                c->st));
+    CUDA_TRY(c, cudaMemsetAsync(c->v, 0, n3 * sizeof(float), c->st));
+    TRY(evaluate(c));
+    k.pde += 2;
+    TRY(absmax3(c, c->grad, &gnorm0));
+    std::swap(c->v, c->vtrial);
+  }
+  TRY(evaluate(c));
+  k.pde += 2;
+  double gn = 0.0;
+  TRY(absmax3(c, c->grad, &gn));
+  if (!std::isfinite(gn)) return fail(c, CLAIRE_ENONFINITE, "gradient is not finite");
+  if (gnorm0 <= 0.0) gnorm0 = gn;
+  if (out->newton_iters == 0 && out->J0 == 0.0) out->J0 = c->J;
+  out->gnorm0 = gnorm0;
+  claire_status result = CLAIRE_OK;
+  int iters = 0;
+  while (iters < c->opt.max_newton) {
+    if (!c->opt.fixed_iters && (gn <= c->opt.eps_opt * gnorm0 || gn <= 1e-6)) break;
+    const double ratio = gn / gnorm0;
+    const double eta = std::fmin(0.5, c->opt.forcing == 0 ? std::sqrt(ratio) : ratio);
+    double gg = 0.0;
+    TRY(dot3(c, c->grad, c->grad, &gg));
+    claire_status curv = CLAIRE_OK;
+    TRY(pcg(c, eta * std::sqrt(gg), k, &curv));
+    double gamma = 0.0;
+    bool ok = false;
+    TRY(armijo(c, k, &gamma, &ok));
+    if (!ok) {
+      result = fail(c, CLAIRE_ELINESEARCH, "Armijo line search failed after 10 halvings");
+      // restore the stored evaluation at the last accepted v
+      TRY(evaluate(c));
+      k.pde += 2;
+      break;
+    }
+    TRY(adjoint_and_gradient(c));
+    ++k.pde;
+    c->have_eval = true;
+    ++iters;
+    ++out->newton_iters;
+    TRY(absmax3(c, c->grad, &gn));
+    if (!std::isfinite(gn)) return fail(c, CLAIRE_ENONFINITE, "gradient is not finite");
+    if (c->opt.verbose)
+      fprintf(stderr, "[claire] beta_v %.3e  it %2d  J %.6e  |g|/|g0| %.3e  pcg %d  step %.3g\n",
+              c->beta_v, out->newton_iters, c->J, gn / gnorm0, k.pcg, gamma);
+  }
+  out->J = c->J;
+  out->grad_rel = gn / gnorm0;
+  if (result == CLAIRE_OK && !c->opt.fixed_iters && gn > c->opt.eps_opt * gnorm0 && gn > 1e-6)
+    result = fail(c, CLAIRE_ENOTCONV, "max_newton reached at relative gradient %.3e",
+                  gn / gnorm0);
+  return result;
+}
+
+bool valid_dims(int nx, int ny, int nz) {
+  auto ok = [](int n) { return n >= 16 && n % 2 == 0; };
+  if (!ok(nx) || !ok(ny) || !ok(nz)) return false;
+  const double N = (double)nx * ny * nz;
+  return 3.0 * N < 2147483647.0;
+}
+
+claire_status finish_stats(claire_ctx* c, claire_stats* st, const Counters& k, float ms,
+                           claire_status s) {
+  if (!st) return s;
+  st->pcg_iters = k.pcg;
+  st->matvecs = k.matvecs;
+  st->pde_solves = k.pde;
+  st->linesearch_halvings = k.halvings;
+  const int64_t N = N_of(c);
+  double mis0 = 0.0;
+  if (reduce(c, N, c->m0, c->m1, RED_SQDIFF, &mis0) == CLAIRE_OK && mis0 > 0.0) {
+    const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
+    st->mismatch_rel = c->dist / (0.5 * h3 * mis0);
+  }
+  st->seconds = ms * 1e-3;
+  st->status = (int)s;
+  return s;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+claire_status claire_default_options(claire_options* o) {
+  if (!o) return CLAIRE_EINVAL;
+  memset(o, 0, sizeof *o);
+  o->precision = 0;
+  o->hessian = 0;
+  o->beta_w = 0.0;
+  o->eps_opt = 5e-2;
+  o->max_newton = 50;
+  o->max_pcg = 100;
+  o->fixed_iters = 0;
+  o->forcing = 0;
+  o->stream = nullptr;
+  o->verbose = 0;
+  o->gnorm0 = 0.0;
+  return CLAIRE_OK;
+}
+
+claire_status claire_destroy(claire_ctx* c) {
+  if (!c) return CLAIRE_OK;
+  c->prof.release();
+  if (c->plans) {
+    cufftDestroy(c->r2c);
+    cufftDestroy(c->c2r);
+  }
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->detf) cudaFree(c->detf);
+  if (c->hres) cudaFreeHost(c->hres);
+  if (c->e0) cudaEventDestroy(c->e0);
+  if (c->e1) cudaEventDestroy(c->e1);
+  delete c;
+  return CLAIRE_OK;
+}
+
+claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, double gamma,
+                            claire_ctx** out) {
+  if (!out) return CLAIRE_EINVAL;
+  *out = nullptr;
+  if (!valid_dims(nx, ny, nz) || nt < 1 || nt > 256 || !(beta_v > 0.0) || !(gamma > 0.0))
+    return CLAIRE_EINVAL;
+  claire_ctx* c = new claire_ctx();
+  claire_default_options(&c->opt);
+  Grid& g = c->g;
+  g.n1 = nx; g.n2 = ny; g.n3 = nz;
+  g.N = (int64_t)nx * ny * nz;
+  const double tp = 2.0 * M_PI;
+  g.h1 = (float)(tp / nx); g.h2 = (float)(tp / ny); g.h3 = (float)(tp / nz);
+  g.inv_h1 = (float)(nx / tp); g.inv_h2 = (float)(ny / tp); g.inv_h3 = (float)(nz / tp);
+  c->nt = nt;
+  c->beta_v = beta_v;
+  c->gamma = gamma;
+  const int64_t N = g.N;
+  claire_status s = CLAIRE_OK;
+  float** fields1[] = {&c->m0, &c->m1, &c->D, &c->cf, &c->pp0, &c->pp1};
+  float** fields3[] = {&c->v, &c->df, &c->db, &c->grad, &c->Lv, &c->scr3, &c->vt, &c->r,
+                       &c->z, &c->s, &c->Hs, &c->vtrial, &c->dtrial};
+  for (auto p : fields1) if (s == CLAIRE_OK) s = alloc(c, p, N);
+  for (auto p : fields3) if (s == CLAIRE_OK) s = alloc(c, p, 3 * N);
+  float** hists[] = {&c->mhist, &c->lhist, &c->shist, &c->lthist};
+  for (auto p : hists) if (s == CLAIRE_OK) s = alloc(c, p, (int64_t)(nt + 1) * N);
+  const int64_t Nc = (int64_t)nx * ny * (nz / 2 + 1);
+  if (s == CLAIRE_OK) {
+    float* cb = nullptr;
+    s = alloc(c, &cb, 3 * Nc * 2);
+    c->cbuf = (cufftComplex*)cb;
+  }
+  if (s == CLAIRE_OK) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (c->red_blocks + 8) * sizeof(double)) != cudaSuccess) {
+      s = CLAIRE_ENOMEM;
+    } else {
+      c->allocs.push_back(p);
+      c->partial = (double*)p;
+      c->dres = c->partial + c->red_blocks;
+    }
+  }
+  if (s == CLAIRE_OK && cudaMallocHost(&c->hres, 8 * sizeof(double)) != cudaSuccess)
+    s = CLAIRE_ENOMEM;
+  if (s == CLAIRE_OK) {
+    int n[3] = {nx, ny, nz};
+    if (cufftPlanMany(&c->r2c, 3, n, nullptr, 1, (int)N, nullptr, 1, (int)Nc, CUFFT_R2C, 3) !=
+            CUFFT_SUCCESS ||
+        cufftPlanMany(&c->c2r, 3, n, nullptr, 1, (int)Nc, nullptr, 1, (int)N, CUFFT_C2R, 3) !=
+            CUFFT_SUCCESS)
+      s = CLAIRE_ECUDA;
+    else
+      c->plans = true;
+  }
+  if (s == CLAIRE_OK && (cudaEventCreate(&c->e0) != cudaSuccess ||
+                         cudaEventCreate(&c->e1) != cudaSuccess))
+    s = CLAIRE_ECUDA;
+  if (s == CLAIRE_OK) {
+    cudaMemset(c->m0, 0, N * sizeof(float));
+    cudaMemset(c->m1, 0, N * sizeof(float));
+    if (cudaDeviceSynchronize() != cudaSuccess) s = CLAIRE_ECUDA;
+  }
+  if (s != CLAIRE_OK) {
+    cudaGetLastError();
+    claire_destroy(c);
+    return s;
+  }
+  *out = c;
+  return CLAIRE_OK;
+}
+
+claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
+  if (!c || !o) return CLAIRE_EINVAL;
+  if (o->precision < 0 || o->precision > 1 || o->hessian < 0 || o->hessian > 1 ||
+      !(o->beta_w >= 0.0) || !(o->eps_opt > 0.0) || o->max_newton < 0 || o->max_pcg < 1 ||
+      o->forcing < 0 || o->forcing > 1)
+    return fail(c, CLAIRE_EINVAL, "invalid option value");
+  if (o->hessian == 1)
+    return fail(c, CLAIRE_EINVAL, "full-Newton Hessian is not available in this build");
+  if (o->precision == 1)
+    return fail(c, CLAIRE_EINVAL, "mixed precision is not available in this build");
+  c->opt = *o;
+  c->st = (cudaStream_t)o->stream;
+  CUFFT_TRY(c, cufftSetStream(c->r2c, c->st));
+  CUFFT_TRY(c, cufftSetStream(c->c2r, c->st));
+  c->have_eval = false;
+  return CLAIRE_OK;
+}
+
+claire_status claire_get_options(const claire_ctx* c, claire_options* o) {
+  if (!c || !o) return CLAIRE_EINVAL;
+  *o = c->opt;
+  return CLAIRE_OK;
+}
+
+claire_status claire_set_beta(claire_ctx* c, double beta_v) {
+  if (!c || !(beta_v > 0.0)) return CLAIRE_EINVAL;
+  c->beta_v = beta_v;
+  c->have_eval = false;
+  return CLAIRE_OK;
+}
+
+size_t claire_workspace_bytes(const claire_ctx* c) { return c ? c->bytes : 0; }
+
+const char* claire_last_error(const claire_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1) {
+  ENTER(c);
+  if (!c || !m0 || !m1) return CLAIRE_EINVAL;
+  const size_t b = N_of(c) * sizeof(float);
+  CUDA_TRY(c, cudaMemcpyAsync(c->m0, m0, b, cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->m1, m1, b, cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->have_eval = false;
+  return CLAIRE_OK;
+}
+
+claire_status claire_transport(claire_ctx* c, const float* v, float* m1_out) {
+  ENTER(c);
+  if (!c || !v || !m1_out) return CLAIRE_EINVAL;
+  const int64_t N = N_of(c);
+  launch_trace(c->g, v, c->dtrial, nullptr, ht_of(c), c->st);
+  const float* src = c->m0;
+  for (int j = 0; j < c->nt; ++j) {
+    float* dst = (j == c->nt - 1) ? m1_out : ((j % 2 == 0) ? c->pp0 : c->pp1);
+    launch_sl(c->g, src, c->dtrial, nullptr, 1.0f, nullptr, 0.0f, dst, c->st);
+    src = dst;
+  }
+  TRY(check_launch(c, "transport"));
+  (void)N;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_objective_gradient(claire_ctx* c, const float* v, double* J, float* g) {
+  ENTER(c);
+  if (!c || !v || !J) return CLAIRE_EINVAL;
+  const size_t b3 = 3 * N_of(c) * sizeof(float);
+  CUDA_TRY(c, cudaMemcpyAsync(c->v, v, b3, cudaMemcpyDeviceToDevice, c->st));
+  TRY(evaluate(c));
+  *J = c->J;
+  if (g) CUDA_TRY(c, cudaMemcpyAsync(g, c->grad, b3, cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_hessian_matvec(claire_ctx* c, const float* vt, float* Hvt) {
+  ENTER(c);
+  if (!c || !vt || !Hvt) return CLAIRE_EINVAL;
+  TRY(matvec(c, vt, Hvt));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+// Continuation over nlev values of beta_v (Sec. 2.6), each level warm-started
+// from the previous one.  v_in / v_out are device pointers, or NULL to use the
+// iterate already held in c->v.
+static claire_status solve_levels(claire_ctx* c, const double* betas, int nlev, const float* v_in,
+                                  float* v_out, claire_stats* st) {
+  if (!c || nlev < 1) return CLAIRE_EINVAL;
+  ENTER(c);
+  for (int i = 0; i < nlev; ++i)
+    if (!(betas[i] > 0.0)) return CLAIRE_EINVAL;
+  claire_stats local{};
+  claire_stats* out = st ? st : &local;
+  memset(out, 0, sizeof *out);
+  Counters k;
+  const size_t b3 = 3 * N_of(c) * sizeof(float);
+  CUDA_TRY(c, cudaEventRecord(c->e0, c->st));
+  if (v_in) CUDA_TRY(c, cudaMemcpyAsync(c->v, v_in, b3, cudaMemcpyDeviceToDevice, c->st));
+  double gnorm0 = c->opt.gnorm0;
+  claire_status s = CLAIRE_OK;
+  for (int i = 0; i < nlev; ++i) {
+    c->beta_v = betas[i];
+    s = gauss_newton(c, gnorm0, k, out);
+    gnorm0 = out->gnorm0;
+    if (s != CLAIRE_OK && s != CLAIRE_ENOTCONV) break;
+  }
+  cudaError_t e = cudaSuccess;
+  if (v_out) e = cudaMemcpyAsync(v_out, c->v, b3, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess) e = cudaEventRecord(c->e1, c->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->e1);
+  if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "solve epilogue: %s", cudaGetErrorString(e));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->e0, c->e1);
+  return finish_stats(c, out, k, ms, s);
+}
+
+claire_status claire_solve(claire_ctx* c, float* v_inout, claire_stats* st) {
+  if (!c || !v_inout) return CLAIRE_EINVAL;
+  const double b = c->beta_v;
+  return solve_levels(c, &b, 1, v_inout, v_inout, st);
+}
+
+claire_status claire_solve_continuation(claire_ctx* c, const double* betas, int nlevels,
+                                        float* v_inout, claire_stats* st) {
+  if (!c || !betas || !v_inout || nlevels < 1) return CLAIRE_EINVAL;
+  return solve_levels(c, betas, nlevels, v_inout, v_inout, st);
+}
+
+claire_status claire_solve_host(claire_ctx* c, const float* m0_host, const float* m1_host,
+                                const double* betas, int nlevels, float* v_inout_host,
+                                claire_stats* st) {
+  if (!c || !m0_host || !m1_host || !v_inout_host) return CLAIRE_EINVAL;
+  if (betas != nullptr && nlevels < 1) return CLAIRE_EINVAL;
+  ENTER(c);
+  const size_t b = N_of(c) * sizeof(float);
+  CUDA_TRY(c, cudaMemcpyAsync(c->m0, m0_host, b, cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->m1, m1_host, b, cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->v, v_inout_host, 3 * b, cudaMemcpyHostToDevice, c->st));
+  c->have_eval = false;
+  const double beta = c->beta_v;
+  claire_status s = betas ? solve_levels(c, betas, nlevels, nullptr, nullptr, st)
+                          : solve_levels(c, &beta, 1, nullptr, nullptr, st);
+  if (s != CLAIRE_OK && s != CLAIRE_ENOTCONV && s != CLAIRE_ELINESEARCH) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(v_inout_host, c->v, 3 * b, cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return s;
+}
+
+claire_status claire_trace(claire_ctx* c, const float* v, float* d_fwd, float* d_bwd) {
+  ENTER(c);
+  if (!c || !v) return CLAIRE_EINVAL;
+  launch_trace(c->g, v, d_fwd, d_bwd, ht_of(c), c->st);
+  TRY(check_launch(c, "trace"));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_interp(claire_ctx* c, const float* u, const float* d, float* out) {
+  ENTER(c);
+  if (!c || !u || !d || !out) return CLAIRE_EINVAL;
+  launch_sl(c->g, u, d, nullptr, 1.0f, nullptr, 0.0f, out, c->st);
+  TRY(check_launch(c, "interp"));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_grad8(claire_ctx* c, const float* u, float* gu) {
+  ENTER(c);
+  if (!c || !u || !gu) return CLAIRE_EINVAL;
+  launch_grad8(c->g, u, gu, c->st);
+  TRY(check_launch(c, "grad8"));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_div8(claire_ctx* c, const float* w, float* dw) {
+  ENTER(c);
+  if (!c || !w || !dw) return CLAIRE_EINVAL;
+  launch_div8(c->g, w, dw, c->st);
+  TRY(check_launch(c, "div8"));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_spectral(claire_ctx* c, int op, const float* in, float* out) {
+  ENTER(c);
+  if (!c || !in || !out || op < 0 || op > 3) return CLAIRE_EINVAL;
+  if (op == CLAIRE_OP_NEAR_INC && !(c->opt.beta_w > 0.0))
+    return fail(c, CLAIRE_EINVAL, "near-incompressible operator needs options.beta_w > 0");
+  TRY(spectral(c, op, in, out, c->beta_v));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_det_deformation_gradient(claire_ctx* c, const float* v, double* mmm,
+                                              float* det_out) {
+  ENTER(c);
+  if (!c || !v || !mmm) return CLAIRE_EINVAL;
+  const int64_t N = N_of(c);
+  if (!c->detf) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)37 * N * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CLAIRE_ENOMEM, "det F workspace allocation failed");
+    }
+    c->detf = (float*)p;
+    c->bytes += (size_t)37 * N * sizeof(float);
+  }
+  float* F = c->detf;
+  float* Fn = F + 9 * N;
+  float* A = Fn + 9 * N;
+  float* Ay = A + 9 * N;
+  float* det = Ay + 9 * N;
+  launch_trace(c->g, v, c->dtrial, nullptr, ht_of(c), c->st);
+  launch_detf(c->g, v, c->dtrial, c->nt, F, Fn, A, Ay, det, c->st);
+  TRY(check_launch(c, "detF"));
+  double mn = 0.0, mx = 0.0, sum = 0.0;
+  TRY(reduce(c, N, det, nullptr, RED_MIN, &mn));
+  TRY(reduce(c, N, det, nullptr, RED_MAX, &mx));
+  TRY(reduce(c, N, det, nullptr, RED_SUM, &sum));
+  mmm[0] = mn;
+  mmm[1] = mx;
+  mmm[2] = sum / (double)N;
+  if (det_out) CUDA_TRY(c, cudaMemcpyAsync(det_out, det, N * sizeof(float),
+                                           cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_profile_reset(claire_ctx* c, int timing) {
+  if (!c) return CLAIRE_EINVAL;
+  ENTER(c);
+  c->prof.reset(timing != 0);
+  return CLAIRE_OK;
+}
+
+int claire_profile_read(claire_ctx* c, claire_kernel_stat* out, int max) {
+  if (!c) return -1;
+  if (c->prof.resolve() != cudaSuccess) return -1;
+  int n = 0;
+  for (int k = 0; k < K_COUNT && (out == nullptr || n < max); ++k, ++n) {
+    if (!out) continue;
+    out[n].name = kernel_kind_name(k);
+    out[n].launches = c->prof.launches[k];
+    out[n].timed = c->prof.timed[k];
+    out[n].bytes = c->prof.bytes[k];
+    out[n].ms = c->prof.ms[k];
+  }
+  return out ? n : (int)K_COUNT;
+}
+
+}  // extern "C"

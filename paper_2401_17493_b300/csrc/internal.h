@@ -1,0 +1,76 @@
+// Internal declarations shared by the kernel launchers and the host solver.
+#pragma once
+
+#include <cufft.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace claire {
+
+// ---- launch accounting and optional per-kernel event timing ---------------
+// Every launcher below counts its launch and the algorithmic bytes it moves
+// (each input field read once, each output written once) in the profiler of
+// the calling context; with timing on it also brackets the launch with a pair
+// of CUDA events on the launch stream.
+enum KernelKind {
+  K_TRACE, K_SL, K_ADJFAC, K_GRAD8, K_DIV8, K_SDOT, K_ACCUM, K_SPECTRAL, K_REDUCE, K_VECTOR,
+  K_DETF, K_CUFFT, K_COUNT
+};
+const char* kernel_kind_name(int k);
+
+struct Profiler {
+  bool timing = false;
+  long long launches[K_COUNT] = {};
+  double bytes[K_COUNT] = {};
+  double ms[K_COUNT] = {};
+  long long timed[K_COUNT] = {};
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  void reset(bool timing_on);
+  cudaEvent_t take();
+  // waits for the recorded events and folds their times into ms[]
+  cudaError_t resolve();
+  void release();
+};
+
+// The profiler of the context whose API call is running on this thread.
+extern thread_local Profiler* tl_prof;
+
+struct ProfileRange {
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfileRange(int k, double bytes, cudaStream_t s);
+  ~ProfileRange();
+};
+
+void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht, cudaStream_t st);
+void launch_sl(const Grid& g, const float* u, const float* d, const float* scale, float sigma,
+               const float* aux, float beta, float* out, cudaStream_t st);
+void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float ht, float* c,
+                           cudaStream_t st);
+void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st);
+void launch_div8(const Grid& g, const float* w, float* out, cudaStream_t st);
+void launch_sdot_hist(const Grid& g, const float* mhist, int nt, const float* vt, float scale0,
+                      float* shist, cudaStream_t st);
+void launch_accum_hist(const Grid& g, const float* lhist, const float* mhist, int nt,
+                       const float* base, float base_coef, float* out, cudaStream_t st);
+void launch_spectral(const Grid& g, cufftComplex* X, int op, float alpha, float gamma,
+                     float beta_w, cudaStream_t st);
+void launch_reduce(int64_t n, const float* a, const float* b, int mode, double* partial,
+                   int nblocks, double* out, cudaStream_t st);
+void launch_axpby(int64_t n, float a, const float* x, float b, float* y, cudaStream_t st);
+void launch_lincomb(int64_t n, float a, const float* x, float b, const float* y, float* out,
+                    cudaStream_t st);
+void launch_detf(const Grid& g, const float* v, const float* df, int nt, float* F, float* Fn,
+                 float* A, float* Ay, float* det, cudaStream_t st);
+
+enum ReduceMode {
+  RED_DOT = 0, RED_SQDIFF = 1, RED_ABSMAX = 2, RED_SQ = 3, RED_MAX = 4, RED_MIN = 5, RED_SUM = 6
+};
+
+}  // namespace claire

@@ -1,0 +1,73 @@
+"""Per-kernel microbenchmark through the C ABI (one kernel per entry point).
+
+    python -m paper_2401_17493_b300.kernel_bench [--size 256] [--reps 20] [--only sl]
+
+Each entry point below launches exactly one of the library's kernels on a
+256^3 grid (fields of 64 MiB, larger than L2), timed with CUDA events on the
+launching stream after warm-up.  GB/s use the algorithmic bytes of the launch
+(each input field read once, each output written once).  Also the command
+profiled by ncu for the per-kernel captures.
+"""
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--only", default=None)
+    args = ap.parse_args()
+    import torch
+    from paper_2401_17493_b300 import build, claire, synth
+    build.build()
+    n = args.size
+    shape = (n, n, n)
+    N = n ** 3
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    u = torch.rand(shape, device="cuda", generator=gen)
+    v = torch.from_numpy(synth.bandlimited_velocity(shape, 8, 4.0, 3).astype(np.float32)).cuda()
+    ctx = claire.Context(shape, nt=4)
+    ctx.set_images(u, u)
+    d, _ = ctx.trace(v)
+    out1 = torch.empty(shape, device="cuda")
+    w = torch.empty((3,) + shape, device="cuda")
+    cases = {
+        "sl": (lambda: ctx.lib.claire_interp(ctx.h, claire._ptr(u), claire._ptr(d),
+                                             claire._ptr(out1)), 20 * N),
+        "trace": (lambda: ctx.lib.claire_trace(ctx.h, claire._ptr(v), claire._ptr(w), None),
+                  24 * N),
+        "grad8": (lambda: ctx.lib.claire_grad8(ctx.h, claire._ptr(u), claire._ptr(w)), 16 * N),
+        "div8": (lambda: ctx.lib.claire_div8(ctx.h, claire._ptr(v), claire._ptr(out1)), 16 * N),
+    }
+    kind = {"sl": "sl_step", "trace": "trace", "grad8": "grad8", "div8": "div8"}
+    res = {}
+    for name, (fn, nbytes) in cases.items():
+        if args.only and name != args.only:
+            continue
+        for _ in range(args.warmup):
+            assert fn() == 0
+        torch.cuda.synchronize()
+        # per-launch CUDA events on the launching stream (the library's profiler)
+        ctx.profile_reset(timing=True)
+        for _ in range(args.reps):
+            assert fn() == 0
+        p = ctx.profile_read()[kind[name]]
+        ms = p["ms"] / p["timed"]
+        res[name] = {"ms": ms, "GB/s": p["bytes"] / p["launches"] / (ms * 1e-3) / 1e9,
+                     "bytes_per_launch": p["bytes"] / p["launches"]}
+    print(json.dumps({"size": n, "kernels": res}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,61 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point declared in include/claire.h; argument validation that needs no
+device (NULL handles)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "claire.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(claire_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_17493_b300 import build
+    build.build()
+    from paper_2401_17493_b300 import claire
+    return claire.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("claire_create", "claire_transport", "claire_objective_gradient",
+                     "claire_hessian_matvec", "claire_solve", "claire_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2401_17493_b300 import claire
+    assert sorted(claire.EXPORTED) == _declared()
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    from paper_2401_17493_b300 import claire
+    assert lib.claire_default_options(None) == claire.EINVAL
+    assert lib.claire_create(64, 64, 64, 4, 1e-2, 1.0, None) == claire.EINVAL
+    h = ctypes.c_void_p()
+    # invalid shapes are rejected before any CUDA call
+    assert lib.claire_create(15, 64, 64, 4, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
+    assert lib.claire_create(64, 8, 64, 4, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
+    assert lib.claire_create(64, 64, 64, 0, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
+    assert lib.claire_create(64, 64, 64, 4, 0.0, 1.0, ctypes.byref(h)) == claire.EINVAL
+    assert h.value is None
+    assert lib.claire_destroy(None) == claire.OK
+    assert lib.claire_last_error(None) == b"null context"
+    o = claire.Options()
+    assert lib.claire_default_options(ctypes.byref(o)) == claire.OK
+    assert abs(o.eps_opt - 5e-2) < 1e-15 and o.max_pcg == 100 and o.hessian == 0
