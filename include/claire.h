@@ -157,6 +157,44 @@ claire_status claire_spectral(claire_ctx* ctx, int op, const float* in, float* o
 claire_status claire_det_deformation_gradient(claire_ctx* ctx, const float* v,
                                               double* minmaxmean_host, float* det_out);
 
+/* ---- allocation-free transport --------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory.  Every other call works through a context
+ * whose workspace comes from cudaMalloc.  Callers whose device memory is
+ * reserved up front by another allocator (a framework's caching allocator, a
+ * fixed pool sized to the GPU) cannot add driver allocations without failing
+ * or fragmenting that pool, and some cannot accept the device-wide
+ * synchronisation that cudaMalloc / cudaFree may imply.
+ *
+ * claire_transport_noalloc computes the same m(1) as claire_transport (RK2
+ * departure points along +v, nt homogeneous SL steps, Sec. 2.5.2) with the same
+ * kernels, without a context and without allocating: no cudaMalloc, no
+ * cudaFree, no allocating library routine.  Its scratch (departure
+ * displacements and one intermediate field, 16 bytes per voxel) is a
+ * file-scope device array sized for CLAIRE_NOALLOC_MAX_VOXELS voxels
+ * (2^20, i.e. 16 MiB), which every GPU that loads the library holds until the
+ * process exits.  Larger grids are rejected with CLAIRE_EINVAL and a message.
+ *
+ *  v       device [3][nx][ny][nz] float32 velocity (caller-owned, read only)
+ *  m0      device [nx][ny][nz] float32 template (read only)
+ *  m1_out  device [nx][ny][nz] float32 output; must not overlap m0 or v
+ *  stream  cudaStream_t (NULL = legacy default stream); the call returns after
+ *          synchronising that stream
+ *  err     optional buffer (may be NULL) that receives a message on failure
+ * Sizes must be even and >= 16, 1 <= nt <= 256.
+ *
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before any stream capture.  All calls in the process share the
+ * one array per device and it keeps the last call's contents (every call
+ * rewrites all of the scratch it reads, so nothing needs clearing); calls that
+ * overlap on the same GPU (other streams or threads) race on it, so callers
+ * must serialise them. */
+#define CLAIRE_NOALLOC_MAX_VOXELS (1LL << 20)
+claire_status claire_transport_noalloc(int nx, int ny, int nz, int nt, const float* v,
+                                       const float* m0, float* m1_out, void* stream,
+                                       char* err, size_t err_len);
+
 /* ---- launch accounting ---------------------------------------------------
  * The context counts every kernel it launches by class, with the algorithmic
  * bytes each launch moves (each input field read once, each output written

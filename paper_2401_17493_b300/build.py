@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libclaire.so")
-SOURCES = ["kernels.cu", "claire_api.cu"]
+SOURCES = ["kernels.cu", "claire_api.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 
 NVCC_FLAGS = [

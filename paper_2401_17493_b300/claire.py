@@ -24,6 +24,7 @@ EXPORTED = [
     "claire_solve_continuation", "claire_solve_host", "claire_destroy", "claire_last_error",
     "claire_trace", "claire_interp", "claire_grad8", "claire_div8", "claire_spectral",
     "claire_det_deformation_gradient", "claire_profile_reset", "claire_profile_read",
+    "claire_transport_noalloc",
 ]
 
 
@@ -100,6 +101,7 @@ def load_library(path=LIB_PATH):
         "claire_det_deformation_gradient": ([P, P, ctypes.POINTER(D), P], I),
         "claire_profile_reset": ([P, I], I),
         "claire_profile_read": ([P, ctypes.POINTER(KernelStat), I], I),
+        "claire_transport_noalloc": ([I, I, I, I, P, P, P, P, ctypes.c_char_p, S], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -121,6 +123,30 @@ def _ptr(t, shape=None, what="array"):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+NOALLOC_MAX_VOXELS = 1 << 20
+
+
+def transport_noalloc(v, m0, out, nt=4, stream=None):
+    """m(1) through claire_transport_noalloc (no device allocation in the library).
+
+    For callers that cannot allocate device memory: the library keeps its
+    scratch in a static device array for up to NOALLOC_MAX_VOXELS voxels, shared
+    by all calls (serialise overlapping calls).  v (3, n1, n2, n3), m0 and out
+    (n1, n2, n3) are caller-owned CUDA float32 tensors."""
+    import torch
+    L = load_library()
+    shape = tuple(m0.shape)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    buf = ctypes.create_string_buffer(512)
+    st = L.claire_transport_noalloc(*shape, int(nt), _ptr(v, (3,) + shape, "v"),
+                                    _ptr(m0, shape, "m0"), _ptr(out, shape, "out"),
+                                    ctypes.c_void_p(stream.cuda_stream), buf, 512)
+    if st != OK:
+        raise ClaireError(st, buf.value.decode())
+    return out
 
 
 class Context:
