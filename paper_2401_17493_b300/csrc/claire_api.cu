@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -34,6 +35,11 @@ struct claire_ctx {
   // matvec and PCG workspace
   float *shist = nullptr, *pp0 = nullptr, *pp1 = nullptr, *lthist = nullptr;
   float *vt = nullptr, *r = nullptr, *z = nullptr, *s = nullptr, *Hs = nullptr;
+  float* hs = nullptr;          // beta_v L s, carried by recurrence inside PCG
+  double* slots = nullptr;      // device FP64 scalars of PCG (see pcg())
+  int* dflag = nullptr;         // device flag: negative curvature / non-finite PCG scalar
+  double* hslots = nullptr;     // pinned host mirror of slots + flag
+  int partial_blocks = 0;
   float *vtrial = nullptr, *dtrial = nullptr;
   cufftComplex* cbuf = nullptr;
   double *partial = nullptr, *dres = nullptr, *hres = nullptr;
@@ -223,9 +229,35 @@ claire_status evaluate(claire_ctx* c) {
 //    w^0 = -(h_t/2) s^0;  w^{j+1} = w^j(y_f) - h_t s^{j+1};  m~(1) = w^{nt-1}(y_f) - (h_t/2) s^nt
 //  incremental adjoint from lam~(1) = -m~(1): lam~^j = c(x) lam~^{j+1}(y_b)
 //  H vt = beta_v L vt + [I - c P_par] sum_j w_j lam~^j grad m^j.
+claire_status matvec_transport(claire_ctx* c, const float* vt);
+
 claire_status matvec(claire_ctx* c, const float* vt, float* Hvt) {
   if (!c->have_eval)
     return fail(c, CLAIRE_EORDER, "hessian_matvec needs a prior objective_gradient");
+  const int64_t N = N_of(c);
+  const Grid& g = c->g;
+  TRY(matvec_transport(c, vt));
+  TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
+  if (c->opt.beta_w > 0.0) {
+    launch_accum_hist(g, c->lthist, c->mhist, c->nt, nullptr, 0.0f, Hvt, c->st);
+    TRY(project_data_term(c, Hvt));
+    TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
+    launch_axpby(3 * N, (float)c->beta_v, c->scr3, 1.0f, Hvt, c->st);
+  } else {
+    launch_accum_hist(g, c->lthist, c->mhist, c->nt, c->scr3, (float)c->beta_v, Hvt, c->st);
+  }
+  return check_launch(c, "matvec accumulate");
+}
+
+// ---------------------------------------------------------------- Krylov / Newton
+
+struct Counters {
+  int pcg = 0, matvecs = 0, pde = 0, halvings = 0;
+};
+
+// Transport part of the Gauss-Newton matvec (incremental state and adjoint):
+// fills lthist with lam~^j for direction vt (see matvec()).
+claire_status matvec_transport(claire_ctx* c, const float* vt) {
   const int64_t N = N_of(c);
   const Grid& g = c->g;
   const float ht = ht_of(c);
@@ -245,66 +277,92 @@ claire_status matvec(claire_ctx* c, const float* vt, float* Hvt) {
   for (int j = nt - 1; j >= 0; --j)
     launch_sl(g, c->lthist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lthist + j * N,
               c->st);
-  TRY(check_launch(c, "matvec transport"));
-  TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
-  if (c->opt.beta_w > 0.0) {
-    launch_accum_hist(g, c->lthist, c->mhist, nt, nullptr, 0.0f, Hvt, c->st);
-    TRY(project_data_term(c, Hvt));
-    TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
-    launch_axpby(3 * N, (float)c->beta_v, c->scr3, 1.0f, Hvt, c->st);
-  } else {
-    launch_accum_hist(g, c->lthist, c->mhist, nt, c->scr3, (float)c->beta_v, Hvt, c->st);
-  }
-  return check_launch(c, "matvec accumulate");
+  return check_launch(c, "matvec transport");
 }
 
-// ---------------------------------------------------------------- Krylov / Newton
+// Slots of the device-side PCG scalars.
+enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4 };
 
-struct Counters {
-  int pcg = 0, matvecs = 0, pde = 0, halvings = 0;
-};
+// z = M^-1 r with M = beta_v L (zero symbol set to one); <r, z> by Parseval into
+// slots[rz_slot] and the component means of r into slots[SLOT_MEAN..+2].
+claire_status precondition(claire_ctx* c, int rz_slot) {
+  const double fft_bytes = 3.0 * (4.0 * c->g.N + 8.0 * c->g.n1 * c->g.n2 * (c->g.n3 / 2 + 1));
+  {
+    ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)c->r, c->cbuf));
+  }
+  launch_spectral(c->g, c->cbuf, CLAIRE_OP_REG_INV, (float)c->beta_v, (float)c->gamma,
+                  (float)c->opt.beta_w, c->st, c->partial, c->slots + SLOT_MEAN);
+  launch_reduce_final(c->partial, spectral_blocks(c->g), RED_SUM, c->slots + rz_slot, c->st);
+  TRY(check_launch(c, "precondition"));
+  {
+    ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    CUFFT_TRY(c, cufftExecC2R(c->c2r, c->cbuf, (cufftReal*)c->z));
+  }
+  return CLAIRE_OK;
+}
 
 // Algorithm 2: PCG for H vt = -g from vt = 0 with M = beta_v L (zero symbol -> 1).
+// The scalars kappa and mu stay on the device (FP64 slots); the regularisation
+// part of H s is carried by the recurrence beta_v L s = (r - mean r) + mu beta_v L s,
+// so each iteration costs one FFT pair (the preconditioner) besides the
+// transport solves.  One host synchronisation per iteration reads <s, H s> and
+// ||r||^2 for the curvature and stopping tests.
 claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
-  const int64_t n3 = 3 * N_of(c);
+  const int64_t N = N_of(c);
+  const int64_t n3 = 3 * N;
+  const Grid& g = c->g;
   *curv = CLAIRE_OK;
+  const int vb = vector_blocks(n3 / 4);
   CUDA_TRY(c, cudaMemsetAsync(c->vt, 0, n3 * sizeof(float), c->st));
+  CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
   launch_lincomb(n3, -1.0f, c->grad, 0.0f, c->grad, c->r, c->st);    // r = -g
-  TRY(spectral(c, CLAIRE_OP_REG_INV, c->r, c->z, c->beta_v));
-  CUDA_TRY(c, cudaMemcpyAsync(c->s, c->z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
-  double rz = 0.0;
-  TRY(dot3(c, c->r, c->z, &rz));
+  int cur = SLOT_RZ0;
+  TRY(precondition(c, cur));
+  launch_s_update(N, c->slots + cur, c->slots + cur, c->slots + SLOT_MEAN, 1, c->z, c->r, c->s,
+                  c->hs, c->st);
+  const bool fused = c->opt.beta_w <= 0.0 && march_supported(c->nt);
   for (int it = 1; it <= c->opt.max_pcg; ++it) {
-    TRY(matvec(c, c->s, c->Hs));
+    TRY(matvec_transport(c, c->s));
+    if (fused) {
+      launch_accum_hist(g, c->lthist, c->mhist, c->nt, c->hs, 1.0f, c->Hs, c->st, c->s,
+                        c->partial);
+      launch_reduce_final(c->partial, march_blocks(g), RED_SUM, c->slots + SLOT_SHS, c->st);
+    } else {
+      launch_accum_hist(g, c->lthist, c->mhist, c->nt, nullptr, 0.0f, c->Hs, c->st);
+      TRY(project_data_term(c, c->Hs));
+      launch_axpby(n3, 1.0f, c->hs, 1.0f, c->Hs, c->st);
+      launch_reduce(n3, c->s, c->Hs, RED_DOT, c->partial, c->red_blocks, c->slots + SLOT_SHS,
+                    c->st);
+    }
     ++k.matvecs;
     k.pde += 2;
-    double sHs = 0.0;
-    TRY(dot3(c, c->s, c->Hs, &sHs));
-    if (!std::isfinite(sHs) || !std::isfinite(rz))
-      return fail(c, CLAIRE_ENONFINITE, "PCG scalar not finite");
-    if (sHs <= 0.0) {                                 // negative curvature (Sec. 2.5.5)
-      *curv = CLAIRE_ENEGCURV;
+    launch_pcg_update(n3, c->slots + cur, c->slots + SLOT_SHS, c->vt, c->r, c->s, c->Hs,
+                      c->partial, vb, c->dflag, c->st);
+    launch_reduce_final(c->partial, vb, RED_SUM, c->slots + SLOT_RR, c->st);
+    TRY(check_launch(c, "pcg update"));
+    CUDA_TRY(c, cudaMemcpyAsync(c->hslots, c->slots, 16 * sizeof(double) + sizeof(int),
+                                cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    const double sHs = c->hslots[SLOT_SHS], rr = c->hslots[SLOT_RR];
+    const int flag = *(const int*)(c->hslots + 16);
+    if (flag) {
+      if (!std::isfinite(sHs) || !std::isfinite(c->hslots[cur]))
+        return fail(c, CLAIRE_ENONFINITE, "PCG scalar not finite");
+      *curv = CLAIRE_ENEGCURV;                     // negative curvature (Sec. 2.5.5)
       if (it == 1)
         CUDA_TRY(c, cudaMemcpyAsync(c->vt, c->s, n3 * sizeof(float), cudaMemcpyDeviceToDevice,
                                     c->st));
       return CLAIRE_OK;
     }
-    const double kappa = rz / sHs;
-    launch_axpby(n3, (float)kappa, c->s, 1.0f, c->vt, c->st);
-    launch_axpby(n3, (float)-kappa, c->Hs, 1.0f, c->r, c->st);
     ++k.pcg;
-    if (!c->opt.fixed_iters) {
-      double rr = 0.0;
-      TRY(reduce(c, n3, c->r, nullptr, RED_SQ, &rr));
-      if (std::sqrt(rr) < tol) break;
-    }
+    if (!c->opt.fixed_iters && std::sqrt(rr) < tol) break;
     if (it == c->opt.max_pcg) break;
-    TRY(spectral(c, CLAIRE_OP_REG_INV, c->r, c->z, c->beta_v));
-    double rz_new = 0.0;
-    TRY(dot3(c, c->z, c->r, &rz_new));
-    const double mu = rz_new / rz;
-    rz = rz_new;
-    launch_axpby(n3, 1.0f, c->z, (float)mu, c->s, c->st);           // s = z + mu s
+    const int nxt = cur == SLOT_RZ0 ? SLOT_RZ1 : SLOT_RZ0;
+    TRY(precondition(c, nxt));
+    launch_s_update(N, c->slots + nxt, c->slots + cur, c->slots + SLOT_MEAN, 0, c->z, c->r,
+                    c->s, c->hs, c->st);
+    cur = nxt;
     TRY(check_launch(c, "pcg"));
   }
   return check_launch(c, "pcg");
@@ -471,6 +529,7 @@ claire_status claire_destroy(claire_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->detf) cudaFree(c->detf);
   if (c->hres) cudaFreeHost(c->hres);
+  if (c->hslots) cudaFreeHost(c->hslots);
   if (c->e0) cudaEventDestroy(c->e0);
   if (c->e1) cudaEventDestroy(c->e1);
   delete c;
@@ -498,7 +557,7 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
   claire_status s = CLAIRE_OK;
   float** fields1[] = {&c->m0, &c->m1, &c->D, &c->cf, &c->pp0, &c->pp1};
   float** fields3[] = {&c->v, &c->df, &c->db, &c->grad, &c->Lv, &c->scr3, &c->vt, &c->r,
-                       &c->z, &c->s, &c->Hs, &c->vtrial, &c->dtrial};
+                       &c->z, &c->s, &c->Hs, &c->hs, &c->vtrial, &c->dtrial};
   for (auto p : fields1) if (s == CLAIRE_OK) s = alloc(c, p, N);
   for (auto p : fields3) if (s == CLAIRE_OK) s = alloc(c, p, 3 * N);
   float** hists[] = {&c->mhist, &c->lhist, &c->shist, &c->lthist};
@@ -510,16 +569,27 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
     c->cbuf = (cufftComplex*)cb;
   }
   if (s == CLAIRE_OK) {
+    // per-block partial sums of every fused reduction share one buffer
+    int pb = c->red_blocks;
+    pb = std::max(pb, spectral_blocks(g));
+    pb = std::max(pb, march_blocks(g));
+    pb = std::max(pb, vector_blocks(3 * N / 4));
+    c->partial_blocks = pb;
     void* p = nullptr;
-    if (cudaMalloc(&p, (c->red_blocks + 8) * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&p, (size_t)(pb + 8 + 16 + 4) * sizeof(double)) != cudaSuccess) {
       s = CLAIRE_ENOMEM;
     } else {
       c->allocs.push_back(p);
       c->partial = (double*)p;
-      c->dres = c->partial + c->red_blocks;
+      c->dres = c->partial + pb;
+      c->slots = c->dres + 8;
+      c->dflag = (int*)(c->slots + 16);
+      c->bytes += (size_t)(pb + 28) * sizeof(double);
     }
   }
   if (s == CLAIRE_OK && cudaMallocHost(&c->hres, 8 * sizeof(double)) != cudaSuccess)
+    s = CLAIRE_ENOMEM;
+  if (s == CLAIRE_OK && cudaMallocHost(&c->hslots, 20 * sizeof(double)) != cudaSuccess)
     s = CLAIRE_ENOMEM;
   if (s == CLAIRE_OK) {
     int n[3] = {nx, ny, nz};

@@ -119,4 +119,18 @@ __device__ __forceinline__ void grad8_at(const float* __restrict__ u, const Grid
   out[2] = fd8(c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], g.inv_h3);
 }
 
+// Asynchronous global -> shared copies (cp.async): all copies of a staging loop
+// are in flight together instead of one load-store round trip per element.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 }  // namespace claire

@@ -57,10 +57,28 @@ void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st);
 void launch_div8(const Grid& g, const float* w, float* out, cudaStream_t st);
 void launch_sdot_hist(const Grid& g, const float* mhist, int nt, const float* vt, float scale0,
                       float* shist, cudaStream_t st);
+// With partial != NULL (nt in {1, 2, 4, 8} only, see march_supported) also
+// writes march_blocks() per-block shares of <dotv, out>.
 void launch_accum_hist(const Grid& g, const float* lhist, const float* mhist, int nt,
-                       const float* base, float base_coef, float* out, cudaStream_t st);
+                       const float* base, float base_coef, float* out, cudaStream_t st,
+                       const float* dotv = nullptr, double* partial = nullptr);
+int march_blocks(const Grid& g);
+bool march_supported(int nt);
+// partial (optional): per-block shares of <in, out>; means (optional): the
+// three component means of the input field.  spectral_blocks() blocks.
 void launch_spectral(const Grid& g, cufftComplex* X, int op, float alpha, float gamma,
-                     float beta_w, cudaStream_t st);
+                     float beta_w, cudaStream_t st, double* partial = nullptr,
+                     double* means = nullptr);
+int spectral_blocks(const Grid& g);
+int vector_blocks(int64_t n);
+void launch_reduce_final(const double* partial, int nblocks, int mode, double* out,
+                         cudaStream_t st);
+void launch_pcg_update(int64_t n, const double* rz, const double* sHs, float* vt, float* r,
+                       const float* s, const float* Hs, double* partial, int nblocks, int* flag,
+                       cudaStream_t st);
+void launch_s_update(int64_t N, const double* rz_new, const double* rz_old, const double* means,
+                     int first, const float* z, const float* r, float* s, float* hs,
+                     cudaStream_t st);
 void launch_reduce(int64_t n, const float* a, const float* b, int mode, double* partial,
                    int nblocks, double* out, cudaStream_t st);
 void launch_axpby(int64_t n, float a, const float* x, float b, float* y, cudaStream_t st);

@@ -16,6 +16,8 @@
 #include <math_constants.h>
 
 #include "internal.h"
+#include "sl_brick.cuh"
+#include "fd8_march.cuh"
 
 namespace claire {
 
@@ -33,68 +35,94 @@ static dim3 grid3(const Grid& g) {
 
 // ---------------------------------------------------------------- trace
 
-__global__ void __launch_bounds__(256) k_trace(Grid g, const float* __restrict__ v,
-                                               float* __restrict__ df, float* __restrict__ db,
-                                               float ht) {
-  CLAIRE_KERNEL_INDEX
+// RK2 departure points of both directions (Sec. 2.5.2) for a tile of nodes.
+// The three velocity components are staged as three bricks (dynamic shared
+// memory); the predictor y~ = x -+ h_t v(x) is interpolated from them, the
+// corrector y = x -+ (h_t / 2)(v(x) + v(y~)) is stored as y - x in grid units.
+__global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __restrict__ v,
+                                                         float* __restrict__ df,
+                                                         float* __restrict__ db, float ht) {
+  extern __shared__ __align__(16) float sm[];
+  const int i1_0 = blockIdx.z * TB1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
   const int64_t N = g.N;
-  const float u1 = v[idx] * g.inv_h1;       // velocity in grid units per unit time
-  const float u2 = v[N + idx] * g.inv_h2;
-  const float u3 = v[2 * N + idx] * g.inv_h3;
-  const int s1 = g.n2 * g.n3;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm + c * BRICK_FLOATS);
+  __syncthreads();
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int i2 = i2_0 + ty, i3 = i3_0 + lane;
+  if (i2 >= g.n2 || i3 >= g.n3) return;
+  const int ctr = (HB_LO * BB2 + ty + HB_LO) * BB3 + lane + HB3_LO;   // node (k = 0) in the brick
+  for (int k = 0; k < TB1; ++k) {
+    const int i1 = i1_0 + k;
+    if (i1 >= g.n1) break;
+    const int64_t idx = lin(g, i1, i2, i3);
+    const int at = ctr + k * BB2 * BB3;
+    const float u1 = sm[at] * g.inv_h1;                       // grid units per unit time
+    const float u2 = sm[BRICK_FLOATS + at] * g.inv_h2;
+    const float u3 = sm[2 * BRICK_FLOATS + at] * g.inv_h3;
 #pragma unroll 1
-  for (int dir = 0; dir < 2; ++dir) {
-    float* out = dir == 0 ? df : db;
-    if (out == nullptr) continue;
-    // transport along +v (dir 0) or -v (dir 1): predictor y~ = x -+ h_t v(x)
-    const float s = dir == 0 ? -ht : ht;
-    Taps a, b, c;
-    axis_taps(i1, s * u1, g.n1, s1, a);
-    axis_taps(i2, s * u2, g.n2, g.n3, b);
-    axis_taps(i3, s * u3, g.n3, 1, c);
-    const float w1 = gather64(v, a, b, c) * g.inv_h1;
-    const float w2 = gather64(v + N, a, b, c) * g.inv_h2;
-    const float w3 = gather64(v + 2 * N, a, b, c) * g.inv_h3;
-    // corrector y = x -+ (h_t / 2)(v(x) + v(y~)), stored as y - x in grid units
-    out[idx] = 0.5f * s * (u1 + w1);
-    out[N + idx] = 0.5f * s * (u2 + w2);
-    out[2 * N + idx] = 0.5f * s * (u3 + w3);
+    for (int dir = 0; dir < 2; ++dir) {
+      float* out = dir == 0 ? df : db;
+      if (out == nullptr) continue;
+      const float sg = dir == 0 ? -ht : ht;                   // transport along +v / -v
+      NodeTaps t;
+      node_taps(sg * u1, sg * u2, sg * u3, t);
+      float w[3];
+      if (taps_in_brick(t)) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[c] = gather_brick(sm + c * BRICK_FLOATS, t, k, ty, lane);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[c] = gather_global(v + c * N, g, t, i1, i2, i3);
+      }
+      out[idx] = 0.5f * sg * (u1 + w[0] * g.inv_h1);
+      out[N + idx] = 0.5f * sg * (u2 + w[1] * g.inv_h2);
+      out[2 * N + idx] = 0.5f * sg * (u3 + w[2] * g.inv_h3);
+    }
   }
 }
 
 // ---------------------------------------------------------------- SL step
 
-__global__ void __launch_bounds__(256) k_sl(Grid g, const float* __restrict__ u,
-                                            const float* __restrict__ d,
-                                            const float* __restrict__ scale, float sigma,
-                                            const float* __restrict__ aux, float beta,
-                                            float* __restrict__ out) {
-  CLAIRE_KERNEL_INDEX
+// MODE 0: out = (scale ? scale(x) : sigma) u(x + d) + beta aux(x)    (SL steps)
+// MODE 1: out = 1 + (h_t/2)(u(y) + u(x) + h_t u(x) u(y)), u = div v: the factor
+//         c(x) with which one RK2 step of d_t lam = lam div v along -v becomes
+//         lam^j(x) = c(x) lam^{j+1}(y).
+template <int MODE>
+__global__ void __launch_bounds__(BRICK_THREADS) k_sl(Grid g, const float* __restrict__ u,
+                                                      const float* __restrict__ d,
+                                                      const float* __restrict__ scale,
+                                                      float sigma,
+                                                      const float* __restrict__ aux, float beta,
+                                                      float ht, float* __restrict__ out) {
+  __shared__ __align__(16) float sm[BRICK_FLOATS];
+  const int i1_0 = blockIdx.z * TB1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+  stage_brick(u, g, i1_0, i2_0, i3_0, sm);
+  __syncthreads();
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int i2 = i2_0 + ty, i3 = i3_0 + lane;
+  if (i2 >= g.n2 || i3 >= g.n3) return;
   const int64_t N = g.N;
-  Taps a, b, c;
-  axis_taps(i1, d[idx], g.n1, g.n2 * g.n3, a);
-  axis_taps(i2, d[N + idx], g.n2, g.n3, b);
-  axis_taps(i3, d[2 * N + idx], g.n3, 1, c);
-  float r = gather64(u, a, b, c);
-  r *= scale ? scale[idx] : sigma;
-  if (aux) r = fmaf(beta, aux[idx], r);
-  out[idx] = r;
-}
-
-// c(x) = 1 + (h_t/2)(D(y) + D(x) + h_t D(x) D(y)): one RK2 step of
-// d_t lam = lam D along -v collapses to lam^j(x) = c(x) lam^{j+1}(y).
-__global__ void __launch_bounds__(256) k_adjoint_factor(Grid g, const float* __restrict__ D,
-                                                        const float* __restrict__ db,
-                                                        float ht, float* __restrict__ cf) {
-  CLAIRE_KERNEL_INDEX
-  const int64_t N = g.N;
-  Taps a, b, c;
-  axis_taps(i1, db[idx], g.n1, g.n2 * g.n3, a);
-  axis_taps(i2, db[N + idx], g.n2, g.n3, b);
-  axis_taps(i3, db[2 * N + idx], g.n3, 1, c);
-  const float Dy = gather64(D, a, b, c);
-  const float Dx = D[idx];
-  cf[idx] = 1.0f + 0.5f * ht * (Dy + Dx + ht * Dx * Dy);
+  const int ctr = (HB_LO * BB2 + ty + HB_LO) * BB3 + lane + HB3_LO;
+#pragma unroll 2
+  for (int k = 0; k < TB1; ++k) {
+    const int i1 = i1_0 + k;
+    if (i1 >= g.n1) break;
+    const int64_t idx = lin(g, i1, i2, i3);
+    NodeTaps t;
+    node_taps(d[idx], d[N + idx], d[2 * N + idx], t);
+    const float y = taps_in_brick(t) ? gather_brick(sm, t, k, ty, lane)
+                                     : gather_global(u, g, t, i1, i2, i3);
+    float r;
+    if (MODE == 1) {
+      const float x = sm[ctr + k * BB2 * BB3];
+      r = 1.0f + 0.5f * ht * (y + x + ht * x * y);
+    } else {
+      r = y * (scale ? scale[idx] : sigma);
+      if (aux) r = fmaf(beta, aux[idx], r);
+    }
+    out[idx] = r;
+  }
 }
 
 // ---------------------------------------------------------------- FD8
@@ -195,50 +223,79 @@ __global__ void __launch_bounds__(256) k_accum_hist(Grid g, const float* __restr
 
 // Half spectrum [n1][n2][n3/2+1] of 3 components (stride Nc).  Integer
 // wavenumbers k_i in FFT order; scale folds in cuFFT's 1/N.
-__global__ void k_spectral(int n1, int n2, int n3, int64_t Nc, cufftComplex* __restrict__ X,
-                           int op, float alpha, float gamma, float beta_w, float scale) {
+// Reduction helpers (defined below with the reductions).
+__device__ __forceinline__ double block_sum(double v);
+
+// Optional fused outputs: partial[blockIdx.x] = this block's share of the real
+// inner product <in, out> by Parseval over the half spectrum (weight 2 for the
+// modes whose conjugates are not stored); means[0..2] = the k = 0 coefficient
+// of each component / N, i.e. the component means of the input field.
+__global__ void __launch_bounds__(256) k_spectral(int n1, int n2, int n3, int64_t Nc,
+                                                  cufftComplex* __restrict__ X, int op,
+                                                  float alpha, float gamma, float beta_w,
+                                                  float scale, double* __restrict__ partial,
+                                                  double* __restrict__ means) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Nc) return;
-  const int nh = n3 / 2 + 1;
-  const int j3 = (int)(i % nh);
-  const int j2 = (int)((i / nh) % n2);
-  const int j1 = (int)(i / ((int64_t)nh * n2));
-  const float k1 = (float)(j1 <= n1 / 2 ? j1 : j1 - n1);
-  const float k2 = (float)(j2 <= n2 / 2 ? j2 : j2 - n2);
-  const float k3 = (float)j3;
-  const float kap = k1 * k1 + k2 * k2 + k3 * k3;
-  cufftComplex x0 = X[i], x1 = X[Nc + i], x2 = X[2 * Nc + i];
-  if (op == 0 || op == 1) {
-    float sig = gamma == 1.0f ? kap : powf(kap, gamma);
-    float f;
-    if (op == 0) {
-      f = sig * scale;                                  // L = (-Laplacian)^gamma
-    } else {
-      if (kap == 0.0f) sig = 1.0f;                      // zero symbol set to one
-      f = scale / (alpha * sig);                        // (alpha L)^-1
-    }
-    x0.x *= f; x0.y *= f; x1.x *= f; x1.y *= f; x2.x *= f; x2.y *= f;
-  } else {
-    // P_par = k k^T / |k|^2 with Nyquist components of k zeroed (real result)
-    const float q1 = (j1 == n1 / 2) ? 0.f : k1;
-    const float q2 = (j2 == n2 / 2) ? 0.f : k2;
-    const float q3 = (j3 == n3 / 2) ? 0.f : k3;
-    const float qq = q1 * q1 + q2 * q2 + q3 * q3;
-    float f = 0.0f;
-    if (qq > 0.0f) {
-      f = scale / qq;
-      if (op == 3) {
-        const float num = beta_w * (1.0f + kap);
-        f *= num / (num + alpha * kap);
+  double dot = 0.0;
+  if (i < Nc) {
+    const int nh = n3 / 2 + 1;
+    const int j3 = (int)(i % nh);
+    const int j2 = (int)((i / nh) % n2);
+    const int j1 = (int)(i / ((int64_t)nh * n2));
+    const float k1 = (float)(j1 <= n1 / 2 ? j1 : j1 - n1);
+    const float k2 = (float)(j2 <= n2 / 2 ? j2 : j2 - n2);
+    const float k3 = (float)j3;
+    const float kap = k1 * k1 + k2 * k2 + k3 * k3;
+    const cufftComplex x0 = X[i], x1 = X[Nc + i], x2 = X[2 * Nc + i];
+    cufftComplex y0, y1, y2;
+    if (op == 0 || op == 1) {
+      float sig = gamma == 1.0f ? kap : powf(kap, gamma);
+      float f;
+      if (op == 0) {
+        f = sig * scale;                                  // L = (-Laplacian)^gamma
+      } else {
+        if (kap == 0.0f) sig = 1.0f;                      // zero symbol set to one
+        f = scale / (alpha * sig);                        // (alpha L)^-1
       }
+      y0 = make_cuComplex(x0.x * f, x0.y * f);
+      y1 = make_cuComplex(x1.x * f, x1.y * f);
+      y2 = make_cuComplex(x2.x * f, x2.y * f);
+    } else {
+      // P_par = k k^T / |k|^2 with Nyquist components of k zeroed (real result)
+      const float q1 = (j1 == n1 / 2) ? 0.f : k1;
+      const float q2 = (j2 == n2 / 2) ? 0.f : k2;
+      const float q3 = (j3 == n3 / 2) ? 0.f : k3;
+      const float qq = q1 * q1 + q2 * q2 + q3 * q3;
+      float f = 0.0f;
+      if (qq > 0.0f) {
+        f = scale / qq;
+        if (op == 3) {
+          const float num = beta_w * (1.0f + kap);
+          f *= num / (num + alpha * kap);
+        }
+      }
+      const float re = (q1 * x0.x + q2 * x1.x + q3 * x2.x) * f;
+      const float im = (q1 * x0.y + q2 * x1.y + q3 * x2.y) * f;
+      y0 = make_cuComplex(q1 * re, q1 * im);
+      y1 = make_cuComplex(q2 * re, q2 * im);
+      y2 = make_cuComplex(q3 * re, q3 * im);
     }
-    const float re = (q1 * x0.x + q2 * x1.x + q3 * x2.x) * f;
-    const float im = (q1 * x0.y + q2 * x1.y + q3 * x2.y) * f;
-    x0.x = q1 * re; x0.y = q1 * im;
-    x1.x = q2 * re; x1.y = q2 * im;
-    x2.x = q3 * re; x2.y = q3 * im;
+    if (partial) {
+      const float w = (j3 == 0 || 2 * j3 == n3) ? 1.0f : 2.0f;
+      dot = (double)(w * (x0.x * y0.x + x0.y * y0.y + x1.x * y1.x + x1.y * y1.y +
+                          x2.x * y2.x + x2.y * y2.y));
+    }
+    if (means && i == 0) {
+      means[0] = (double)x0.x * (double)scale;
+      means[1] = (double)x1.x * (double)scale;
+      means[2] = (double)x2.x * (double)scale;
+    }
+    X[i] = y0; X[Nc + i] = y1; X[2 * Nc + i] = y2;
   }
-  X[i] = x0; X[Nc + i] = x1; X[2 * Nc + i] = x2;
+  if (partial) {
+    const double b = block_sum(dot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = b;
+  }
 }
 
 // ---------------------------------------------------------------- reductions
@@ -277,38 +334,135 @@ __device__ __forceinline__ double warp_red(int mode, double v) {
   return v;
 }
 
+// Block-wide reduction; the result is valid in thread (0, 0).  Works for 1D
+// and 2D blocks (linear thread id); call once per kernel by every thread.
 __device__ __forceinline__ double block_red(int mode, double acc) {
   __shared__ double sh[32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
   acc = warp_red(mode, acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  if ((tid & 31) == 0) sh[tid >> 5] = acc;
   __syncthreads();
   double v = red_init(mode);
-  if (threadIdx.x < 32) {
-    v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : red_init(mode);
+  if (tid < 32) {
+    v = tid < nwarps ? sh[tid] : red_init(mode);
     v = warp_red(mode, v);
   }
   return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) { return block_red(0, v); }
+
+// Each thread folds 4 elements (one float4 per operand) in FP32, then adds the
+// chunk to an FP64 accumulator: FP64 work is 1/4 per element (B300's FP64 rate
+// is low) while the rounding stays at FP32 level per chunk of 4.
+__device__ __forceinline__ float red_term(int mode, float x, float y) {
+  switch (mode) {
+    case 0: return x * y;
+    case 1: { const float d = x - y; return d * d; }
+    case 2: return fabsf(x);
+    case 3: return x * x;
+    default: return x;
+  }
+}
+
+__device__ __forceinline__ float red_chunk(int mode, float a, float b, float c, float d) {
+  if (mode == 2 || mode == 4) return fmaxf(fmaxf(a, b), fmaxf(c, d));
+  if (mode == 5) return fminf(fminf(a, b), fminf(c, d));
+  return (a + b) + (c + d);
 }
 
 __global__ void __launch_bounds__(256) k_reduce(int64_t n, const float* __restrict__ a,
                                                 const float* __restrict__ b, int mode,
                                                 double* __restrict__ partial) {
   double acc = red_init(mode);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = a[i];
-    double t;
-    switch (mode) {
-      case 0: t = x * (double)b[i]; break;
-      case 1: { const double d = x - (double)b[i]; t = d * d; } break;
-      case 2: t = fabs(x); break;
-      case 3: t = x * x; break;
-      default: t = x;
-    }
-    acc = red_combine(mode, acc, t);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+  const int64_t n4 = vec ? n / 4 : 0;
+  for (int64_t i = t0; i < n4; i += stride) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(a) + i);
+    const float4 y = b ? __ldg(reinterpret_cast<const float4*>(b) + i) : x;
+    float c = red_chunk(mode, red_term(mode, x.x, y.x), red_term(mode, x.y, y.y),
+                        red_term(mode, x.z, y.z), red_term(mode, x.w, y.w));
+    // keep a NaN visible to the max / min modes (fmaxf drops it)
+    if ((mode == 2 || mode == 4 || mode == 5) &&
+        (x.x != x.x || x.y != x.y || x.z != x.z || x.w != x.w))
+      c = __int_as_float(0x7fffffff);
+    acc = red_combine(mode, acc, (double)c);
+  }
+  for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
+    const float x = a[i], y = b ? b[i] : x;
+    acc = red_combine(mode, acc, (double)red_term(mode, x, y));
   }
   const double v = block_red(mode, acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = v;
+}
+
+// ---------------------------------------------------------------- PCG vectors
+
+// Algorithm 2 update with device-side scalars: kappa = <r,z> / <s,Hs>;
+// vt += kappa s, r -= kappa Hs, partial ||r||^2.  <s, Hs> <= 0 (negative
+// curvature, Sec. 2.5.5) or a non-finite scalar leaves vt and r untouched and
+// raises *flag.
+__global__ void __launch_bounds__(256) k_pcg_update(int64_t n4, const double* __restrict__ rz,
+                                                    const double* __restrict__ sHs,
+                                                    float4* __restrict__ vt,
+                                                    float4* __restrict__ r,
+                                                    const float4* __restrict__ s,
+                                                    const float4* __restrict__ Hs,
+                                                    double* __restrict__ partial,
+                                                    int* __restrict__ flag) {
+  const double q = *sHs, p = *rz;
+  const bool ok = q > 0.0 && isfinite(q) && isfinite(p);
+  const float kappa = ok ? (float)(p / q) : 0.0f;
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) *flag = 1;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4 rv = r[i];
+    if (ok) {
+      const float4 sv = s[i], hv = Hs[i];
+      float4 v = vt[i];
+      v.x = fmaf(kappa, sv.x, v.x); v.y = fmaf(kappa, sv.y, v.y);
+      v.z = fmaf(kappa, sv.z, v.z); v.w = fmaf(kappa, sv.w, v.w);
+      vt[i] = v;
+      rv.x = fmaf(-kappa, hv.x, rv.x); rv.y = fmaf(-kappa, hv.y, rv.y);
+      rv.z = fmaf(-kappa, hv.z, rv.z); rv.w = fmaf(-kappa, hv.w, rv.w);
+      r[i] = rv;
+    }
+    acc += (double)((rv.x * rv.x + rv.y * rv.y) + (rv.z * rv.z + rv.w * rv.w));
+  }
+  const double b = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
+// mu = rz_new / rz_old (0 on the first iteration): s = z + mu s and the
+// regularisation part of H s by recurrence, hs = (r - mean(r)) + mu hs, since
+// beta_v L z = r - mean(r) for z = (beta_v L)^-1 r with the zero symbol set to one.
+__global__ void __launch_bounds__(256) k_s_update(int64_t n4, int64_t N4,
+                                                  const double* __restrict__ rz_new,
+                                                  const double* __restrict__ rz_old,
+                                                  const double* __restrict__ means, int first,
+                                                  const float4* __restrict__ z,
+                                                  const float4* __restrict__ r,
+                                                  float4* __restrict__ s,
+                                                  float4* __restrict__ hs) {
+  const float mu = first ? 0.0f : (float)(*rz_new / *rz_old);
+  const float m[3] = {(float)means[0], (float)means[1], (float)means[2]};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float mc = m[i / N4];
+    const float4 zv = z[i], rv = r[i];
+    float4 sv = first ? make_float4(0.f, 0.f, 0.f, 0.f) : s[i];
+    float4 hv = first ? make_float4(0.f, 0.f, 0.f, 0.f) : hs[i];
+    sv.x = fmaf(mu, sv.x, zv.x); sv.y = fmaf(mu, sv.y, zv.y);
+    sv.z = fmaf(mu, sv.z, zv.z); sv.w = fmaf(mu, sv.w, zv.w);
+    hv.x = fmaf(mu, hv.x, rv.x - mc); hv.y = fmaf(mu, hv.y, rv.y - mc);
+    hv.z = fmaf(mu, hv.z, rv.z - mc); hv.w = fmaf(mu, hv.w, rv.w - mc);
+    s[i] = sv;
+    hs[i] = hv;
+  }
 }
 
 __global__ void k_reduce_final(const double* __restrict__ partial, int nb, int mode,
@@ -498,20 +652,26 @@ static int vec_blocks(int64_t n) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+static const size_t kTraceSmem = 3 * BRICK_FLOATS * sizeof(float);
 void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht,
                   cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTraceSmem);
+    attr = true;
+  }
   ProfileRange pr(K_TRACE, (double)g.N * (12 + 12 * ((df != nullptr) + (db != nullptr))), st);
-  k_trace<<<grid3(g), block3(), 0, st>>>(g, v, df, db, ht);
+  k_trace<<<brick_grid(g), dim3(32, TB2), kTraceSmem, st>>>(g, v, df, db, ht);
 }
 void launch_sl(const Grid& g, const float* u, const float* d, const float* scale, float sigma,
                const float* aux, float beta, float* out, cudaStream_t st) {
   ProfileRange pr(K_SL, (double)g.N * (20 + 4 * (scale != nullptr) + 4 * (aux != nullptr)), st);
-  k_sl<<<grid3(g), block3(), 0, st>>>(g, u, d, scale, sigma, aux, beta, out);
+  k_sl<0><<<brick_grid(g), dim3(32, TB2), 0, st>>>(g, u, d, scale, sigma, aux, beta, 0.f, out);
 }
 void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float ht, float* c,
                            cudaStream_t st) {
   ProfileRange pr(K_ADJFAC, (double)g.N * 20, st);
-  k_adjoint_factor<<<grid3(g), block3(), 0, st>>>(g, D, db, ht, c);
+  k_sl<1><<<brick_grid(g), dim3(32, TB2), 0, st>>>(g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c);
 }
 void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st) {
   ProfileRange pr(K_GRAD8, (double)g.N * 16, st);
@@ -521,23 +681,81 @@ void launch_div8(const Grid& g, const float* w, float* out, cudaStream_t st) {
   ProfileRange pr(K_DIV8, (double)g.N * 16, st);
   k_div8<<<grid3(g), block3(), 0, st>>>(g, w, out);
 }
+// History FD8 kernels: the marching version for nt in {1, 2, 4, 8}, the
+// per-node global-memory version for any other nt.
+template <int MODE>
+static bool launch_march(const Grid& g, const float* mhist, const float* lhist, const float* vt,
+                         float scale0, const float* base, float base_coef, float* out, int nt,
+                         cudaStream_t st, const float* dotv = nullptr,
+                         double* partial = nullptr) {
+  const dim3 grid = march_grid(g), block(32, MT2);
+#define CLAIRE_MARCH(NF)                                                                  \
+  k_hist_march<MODE, NF><<<grid, block, 0, st>>>(g, mhist, lhist, vt, scale0, base,       \
+                                                 base_coef, out, dotv, partial)
+  switch (nt) {
+    case 1: CLAIRE_MARCH(2); return true;
+    case 2: CLAIRE_MARCH(3); return true;
+    case 4: CLAIRE_MARCH(5); return true;
+    case 8: CLAIRE_MARCH(9); return true;
+    default: return false;
+  }
+#undef CLAIRE_MARCH
+}
+
+int march_blocks(const Grid& g) {
+  const dim3 m = march_grid(g);
+  return (int)(m.x * m.y * m.z);
+}
+bool march_supported(int nt) { return nt == 1 || nt == 2 || nt == 4 || nt == 8; }
+
 void launch_sdot_hist(const Grid& g, const float* mhist, int nt, const float* vt, float scale0,
                       float* shist, cudaStream_t st) {
   ProfileRange pr(K_SDOT, (double)g.N * (12 + 8 * (nt + 1)), st);
-  k_sdot_hist<<<grid3(g), block3(), 0, st>>>(g, mhist, nt, vt, scale0, shist);
+  if (!launch_march<0>(g, mhist, nullptr, vt, scale0, nullptr, 0.f, shist, nt, st))
+    k_sdot_hist<<<grid3(g), block3(), 0, st>>>(g, mhist, nt, vt, scale0, shist);
 }
 void launch_accum_hist(const Grid& g, const float* lhist, const float* mhist, int nt,
-                       const float* base, float base_coef, float* out, cudaStream_t st) {
-  ProfileRange pr(K_ACCUM, (double)g.N * (8 * (nt + 1) + 12 + 12 * (base != nullptr)), st);
-  k_accum_hist<<<grid3(g), block3(), 0, st>>>(g, lhist, mhist, nt, base, base_coef, out);
+                       const float* base, float base_coef, float* out, cudaStream_t st,
+                       const float* dotv, double* partial) {
+  ProfileRange pr(K_ACCUM, (double)g.N * (8 * (nt + 1) + 12 + 12 * (base != nullptr) +
+                                          12 * (partial != nullptr)), st);
+  if (!launch_march<1>(g, mhist, lhist, nullptr, 0.f, base, base_coef, out, nt, st, dotv,
+                       partial))
+    k_accum_hist<<<grid3(g), block3(), 0, st>>>(g, lhist, mhist, nt, base, base_coef, out);
+}
+int spectral_blocks(const Grid& g) {
+  const int64_t Nc = (int64_t)g.n1 * g.n2 * (g.n3 / 2 + 1);
+  return (int)((Nc + 255) / 256);
 }
 void launch_spectral(const Grid& g, cufftComplex* X, int op, float alpha, float gamma,
-                     float beta_w, cudaStream_t st) {
+                     float beta_w, cudaStream_t st, double* partial, double* means) {
   const int64_t Nc = (int64_t)g.n1 * g.n2 * (g.n3 / 2 + 1);
   const float scale = (float)(1.0 / (double)g.N);
   ProfileRange pr(K_SPECTRAL, (double)Nc * 3 * 16, st);
-  k_spectral<<<(unsigned)((Nc + 255) / 256), 256, 0, st>>>(g.n1, g.n2, g.n3, Nc, X, op, alpha,
-                                                           gamma, beta_w, scale);
+  k_spectral<<<spectral_blocks(g), 256, 0, st>>>(g.n1, g.n2, g.n3, Nc, X, op, alpha, gamma,
+                                                 beta_w, scale, partial, means);
+}
+int vector_blocks(int64_t n) { return vec_blocks(n); }
+void launch_reduce_final(const double* partial, int nblocks, int mode, double* out,
+                         cudaStream_t st) {
+  ProfileRange pr(K_REDUCE, (double)nblocks * 8, st);
+  k_reduce_final<<<1, 1024, 0, st>>>(partial, nblocks, mode, out);
+}
+void launch_pcg_update(int64_t n, const double* rz, const double* sHs, float* vt, float* r,
+                       const float* s, const float* Hs, double* partial, int nblocks, int* flag,
+                       cudaStream_t st) {
+  ProfileRange pr(K_VECTOR, (double)n * 24, st);
+  k_pcg_update<<<nblocks, 256, 0, st>>>(n / 4, rz, sHs, (float4*)vt, (float4*)r,
+                                        (const float4*)s, (const float4*)Hs, partial, flag);
+}
+void launch_s_update(int64_t N, const double* rz_new, const double* rz_old, const double* means,
+                     int first, const float* z, const float* r, float* s, float* hs,
+                     cudaStream_t st) {
+  const int64_t n = 3 * N;
+  ProfileRange pr(K_VECTOR, (double)n * (first ? 16 : 24), st);
+  k_s_update<<<vec_blocks(n / 4), 256, 0, st>>>(n / 4, N / 4, rz_new, rz_old, means, first,
+                                                 (const float4*)z, (const float4*)r,
+                                                 (float4*)s, (float4*)hs);
 }
 void launch_reduce(int64_t n, const float* a, const float* b, int mode, double* partial,
                    int nblocks, double* out, cudaStream_t st) {
@@ -562,7 +780,7 @@ void launch_detf(const Grid& g, const float* v, const float* df, int nt, float* 
     k_detf_init<<<grid3(g), block3(), 0, st>>>(g, v, A, F);
   }
   for (int k = 0; k < 9; ++k)
-    launch_sl(g, A + k * g.N, df, nullptr, 1.0f, nullptr, 0.f, Ay + k * g.N, st);
+    launch_sl(g, A + k * g.N, df, nullptr, 1.0f, nullptr, 0.f, Ay + k * g.N, st);  // A(y)
   const float ht = 1.0f / nt;
   for (int j = 0; j < nt; ++j) {
     ProfileRange pr(K_DETF, (double)g.N * (12 + 36 * 4 + (j == nt - 1 ? 4 : 0)), st);

@@ -41,6 +41,8 @@ def main():
     d, _ = ctx.trace(v)
     out1 = torch.empty(shape, device="cuda")
     w = torch.empty((3,) + shape, device="cuda")
+    vt = torch.from_numpy(synth.bandlimited_velocity(shape, 8, 1.0, 5).astype(np.float32)).cuda()
+    ctx.objective_gradient(0.5 * v, want_gradient=False)     # state history for the matvec
     cases = {
         "sl": (lambda: ctx.lib.claire_interp(ctx.h, claire._ptr(u), claire._ptr(d),
                                              claire._ptr(out1)), 20 * N),
@@ -48,8 +50,12 @@ def main():
                   24 * N),
         "grad8": (lambda: ctx.lib.claire_grad8(ctx.h, claire._ptr(u), claire._ptr(w)), 16 * N),
         "div8": (lambda: ctx.lib.claire_div8(ctx.h, claire._ptr(v), claire._ptr(out1)), 16 * N),
+        # one Gauss-Newton matvec: sdot_hist, 8 SL steps, accum_hist, spectral, cufft
+        "matvec": (lambda: ctx.lib.claire_hessian_matvec(ctx.h, claire._ptr(vt), claire._ptr(w)),
+                   None),
     }
-    kind = {"sl": "sl_step", "trace": "trace", "grad8": "grad8", "div8": "div8"}
+    kind = {"sl": "sl_step", "trace": "trace", "grad8": "grad8", "div8": "div8",
+            "matvec": None}
     res = {}
     for name, (fn, nbytes) in cases.items():
         if args.only and name != args.only:
@@ -61,7 +67,16 @@ def main():
         ctx.profile_reset(timing=True)
         for _ in range(args.reps):
             assert fn() == 0
-        p = ctx.profile_read()[kind[name]]
+        prof = ctx.profile_read()
+        if kind[name] is None:          # report every kernel class the call launched
+            for k, p in prof.items():
+                if p["timed"]:
+                    ms = p["ms"] / p["timed"]
+                    res[f"{name}/{k}"] = {"ms_per_launch": ms,
+                                          "launches_per_call": p["launches"] / args.reps,
+                                          "GB/s": p["bytes"] / p["launches"] / (ms * 1e-3) / 1e9}
+            continue
+        p = prof[kind[name]]
         ms = p["ms"] / p["timed"]
         res[name] = {"ms": ms, "GB/s": p["bytes"] / p["launches"] / (ms * 1e-3) / 1e9,
                      "bytes_per_launch": p["bytes"] / p["launches"]}
