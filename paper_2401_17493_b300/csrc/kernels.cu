@@ -36,48 +36,45 @@ static dim3 grid3(const Grid& g) {
 // ---------------------------------------------------------------- trace
 
 // RK2 departure points of both directions (Sec. 2.5.2) for a tile of nodes.
-// The three velocity components are staged as three bricks (dynamic shared
-// memory); the predictor y~ = x -+ h_t v(x) is interpolated from them, the
-// corrector y = x -+ (h_t / 2)(v(x) + v(y~)) is stored as y - x in grid units.
+// The velocity components are staged one at a time into one brick; the
+// predictor y~ = x -+ h_t v(x) is interpolated from it, and the corrector
+// y = x -+ (h_t / 2)(v(x) + v(y~)) is stored as y - x in grid units.
 __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __restrict__ v,
                                                          float* __restrict__ df,
                                                          float* __restrict__ db, float ht) {
   extern __shared__ __align__(16) float sm[];
   const int i1_0 = blockIdx.z * TB1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
   const int64_t N = g.N;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm + c * BRICK_FLOATS);
-  __syncthreads();
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
-  if (i2 >= g.n2 || i3 >= g.n3) return;
-  const int ctr = (HB_LO * BB2 + ty + HB_LO) * BB3 + lane + HB3_LO;   // node (k = 0) in the brick
-  for (int k = 0; k < TB1; ++k) {
-    const int i1 = i1_0 + k;
-    if (i1 >= g.n1) break;
-    const int64_t idx = lin(g, i1, i2, i3);
-    const int at = ctr + k * BB2 * BB3;
-    const float u1 = sm[at] * g.inv_h1;                       // grid units per unit time
-    const float u2 = sm[BRICK_FLOATS + at] * g.inv_h2;
-    const float u3 = sm[2 * BRICK_FLOATS + at] * g.inv_h3;
+  const bool active = i2 < g.n2 && i3 < g.n3;
+  const int kmax = min(TB1, g.n1 - i1_0);
+  bool first = true;
 #pragma unroll 1
-    for (int dir = 0; dir < 2; ++dir) {
-      float* out = dir == 0 ? df : db;
-      if (out == nullptr) continue;
-      const float sg = dir == 0 ? -ht : ht;                   // transport along +v / -v
-      NodeTaps t;
-      node_taps(sg * u1, sg * u2, sg * u3, t);
-      float w[3];
-      if (taps_in_brick(t)) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w[c] = gather_brick(sm + c * BRICK_FLOATS, t, k, ty, lane);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w[c] = gather_global(v + c * N, g, t, i1, i2, i3);
+  for (int dir = 0; dir < 2; ++dir) {
+    float* out = dir == 0 ? df : db;
+    if (out == nullptr) continue;
+    const float sg = dir == 0 ? -ht : ht;        // transport along +v / -v
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      if (!first) __syncthreads();               // previous brick consumed
+      first = false;
+      stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm);
+      __syncthreads();
+      if (!active) continue;
+      const float ihc = c == 0 ? g.inv_h1 : (c == 1 ? g.inv_h2 : g.inv_h3);
+#pragma unroll 2
+      for (int k = 0; k < kmax; ++k) {
+        const int64_t idx = lin(g, i1_0 + k, i2, i3);
+        const float u1 = v[idx] * g.inv_h1, u2 = v[N + idx] * g.inv_h2,
+                    u3 = v[2 * N + idx] * g.inv_h3;    // v(x), grid units per unit time
+        NodeTaps t;
+        node_taps(sg * u1, sg * u2, sg * u3, t);
+        const float w = taps_in_brick(t) ? gather_brick(sm, t, k, ty, lane)
+                                         : gather_global(v + c * N, g, t, i1_0 + k, i2, i3);
+        const float uc = c == 0 ? u1 : (c == 1 ? u2 : u3);
+        out[c * N + idx] = 0.5f * sg * (uc + w * ihc);
       }
-      out[idx] = 0.5f * sg * (u1 + w[0] * g.inv_h1);
-      out[N + idx] = 0.5f * sg * (u2 + w[1] * g.inv_h2);
-      out[2 * N + idx] = 0.5f * sg * (u3 + w[2] * g.inv_h3);
     }
   }
 }
@@ -95,7 +92,7 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl(Grid g, const float* __res
                                                       float sigma,
                                                       const float* __restrict__ aux, float beta,
                                                       float ht, float* __restrict__ out) {
-  __shared__ __align__(16) float sm[BRICK_FLOATS];
+  extern __shared__ __align__(16) float sm[];
   const int i1_0 = blockIdx.z * TB1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
   stage_brick(u, g, i1_0, i2_0, i3_0, sm);
   __syncthreads();
@@ -652,26 +649,35 @@ static int vec_blocks(int64_t n) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-static const size_t kTraceSmem = 3 * BRICK_FLOATS * sizeof(float);
+static const size_t kTraceSmem = BRICK_FLOATS * sizeof(float);
+static const size_t kBrickSmem = BRICK_FLOATS * sizeof(float);
+static void brick_attributes() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTraceSmem);
+  cudaFuncSetAttribute(k_sl<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBrickSmem);
+  cudaFuncSetAttribute(k_sl<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBrickSmem);
+  done = true;
+}
 void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht,
                   cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTraceSmem);
-    attr = true;
-  }
+  brick_attributes();
   ProfileRange pr(K_TRACE, (double)g.N * (12 + 12 * ((df != nullptr) + (db != nullptr))), st);
   k_trace<<<brick_grid(g), dim3(32, TB2), kTraceSmem, st>>>(g, v, df, db, ht);
 }
 void launch_sl(const Grid& g, const float* u, const float* d, const float* scale, float sigma,
                const float* aux, float beta, float* out, cudaStream_t st) {
   ProfileRange pr(K_SL, (double)g.N * (20 + 4 * (scale != nullptr) + 4 * (aux != nullptr)), st);
-  k_sl<0><<<brick_grid(g), dim3(32, TB2), 0, st>>>(g, u, d, scale, sigma, aux, beta, 0.f, out);
+  brick_attributes();
+  k_sl<0><<<brick_grid(g), dim3(32, TB2), kBrickSmem, st>>>(g, u, d, scale, sigma, aux, beta,
+                                                             0.f, out);
 }
 void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float ht, float* c,
                            cudaStream_t st) {
   ProfileRange pr(K_ADJFAC, (double)g.N * 20, st);
-  k_sl<1><<<brick_grid(g), dim3(32, TB2), 0, st>>>(g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c);
+  brick_attributes();
+  k_sl<1><<<brick_grid(g), dim3(32, TB2), kBrickSmem, st>>>(g, D, db, nullptr, 1.f, nullptr,
+                                                             0.f, ht, c);
 }
 void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st) {
   ProfileRange pr(K_GRAD8, (double)g.N * 16, st);

@@ -21,8 +21,12 @@ constexpr int HB_LO = 3, HB_HI = 3;            // x1 / x2 halo: floor(d) in [-2,
 constexpr int HB3_LO = 4, HB3_HI = 4;          // x3 halo (float4 aligned): floor(d) in [-3, 2]
 constexpr int BB1 = TB1 + HB_LO + HB_HI;       // 14
 constexpr int BB2 = TB2 + HB_LO + HB_HI;       // 14
-constexpr int BB3 = TB3 + HB3_LO + HB3_HI;     // 40
-constexpr int BRICK_FLOATS = BB1 * BB2 * BB3;  // 7840 floats = 30.6 KiB
+constexpr int BX3 = TB3 + HB3_LO + HB3_HI;     // 40 staged floats per row
+// Row pitch 64 floats: row and plane strides are multiples of the 32 banks, so
+// lanes whose displacement floors put them in different rows or planes read
+// disjoint banks (only an x3 span wider than 32 words can still conflict).
+constexpr int BB3 = 64;
+constexpr int BRICK_FLOATS = BB1 * BB2 * BB3;  // 12544 floats = 49 KiB
 constexpr int BRICK_THREADS = 32 * TB2;        // 256
 
 __host__ inline dim3 brick_grid(const Grid& g) {
@@ -34,9 +38,9 @@ __device__ __forceinline__ void stage_brick(const float* __restrict__ u, const G
                                             int i2_0, int i3_0, float* __restrict__ s) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const int x3s = i3_0 - HB3_LO;
-  const bool vec = (g.n3 % 4 == 0) && x3s >= 0 && x3s + BB3 <= g.n3 &&
+  const bool vec = (g.n3 % 4 == 0) && x3s >= 0 && x3s + BX3 <= g.n3 &&
                    ((reinterpret_cast<uintptr_t>(u) & 15) == 0);
-  constexpr int Q = BB3 / 4;                         // float4 per row
+  constexpr int Q = BX3 / 4;                         // float4 per staged row
   for (int item = tid; item < BB1 * BB2 * Q; item += BRICK_THREADS) {
     const int row = item / Q, q = item - row * Q;
     const int r1 = row / BB2, r2 = row - r1 * BB2;
