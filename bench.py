@@ -231,6 +231,33 @@ def run_claire(args, world, rank, local):
     s_per_solve = t_max / 1e3 / (args.steps * world)
     launches_per_step = sum(p["launches"] for k, p in prof.items() if k != "cufft") / args.steps
 
+    # mixed-precision form (FP16 field storage): same protocol, same accuracy criteria
+    v_fp32 = v.clone()
+    ctx.set_options(precision=1)
+    vm = torch.zeros_like(v)
+    for _ in range(args.warmup):
+        vm.zero_()
+        ctx.solve_continuation(BETAS, vm)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    mstats = []
+    for _ in range(args.steps):
+        vm.zero_()
+        _, stm = ctx.solve_continuation(BETAS, vm)
+        mstats.append(stm.as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    mixed_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    mixed = {"value": mixed_s, "unit": "s", "speedup_vs_fp32": (t_max / 1e3 / args.steps) / mixed_s,
+             "grad_rel": mstats[-1]["grad_rel"], "mismatch_rel": mstats[-1]["mismatch_rel"],
+             "matvecs": mstats[-1]["matvecs"], "status": mstats[-1]["status"],
+             "v_rel_diff_vs_fp32": float(torch.linalg.vector_norm(vm - v_fp32) /
+                                         torch.linalg.vector_norm(v_fp32)),
+             "storage": "fp16 fields, fp32 math/coordinates/PCG vectors, fp64 reductions"}
+    ctx.set_options(precision=0)
+
     # Hessian matvecs/s at the converged point (50 back-to-back GN matvecs)
     J, _ = ctx.objective_gradient(v, want_gradient=False)
     vt = torch.randn((3,) + shape, device="cuda") * 1e-2
@@ -291,6 +318,7 @@ def run_claire(args, world, rank, local):
                    "l2": "working set ~%.1f GB > 126 MB L2" % (ctx.workspace_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "matvecs_per_s": matvecs_per_s,
+        "mixed": mixed,
         "interp_fd_hbm_frac": interp_gbs / peak,
         "interp_fd_gbs": interp_gbs,
         "solve": {"newton_iters": st0["newton_iters"], "pcg_iters": st0["pcg_iters"],

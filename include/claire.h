@@ -59,6 +59,9 @@ typedef struct {
   int verbose;          /* 1: one line per Newton iteration on stderr                */
   double gnorm0;        /* > 0: denominator of the relative gradient; <= 0: use
                            ||g(v = 0)||_inf computed by the solver (reading C-10)    */
+  int autotune;         /* 1: time the tile-shape variants on the first evaluation of a
+                           solve and keep the fastest for this context (default 0)   */
+  int graphs;           /* 1: replay each PCG iteration as a captured CUDA graph      */
 } claire_options;
 
 typedef struct {
@@ -194,6 +197,29 @@ claire_status claire_det_deformation_gradient(claire_ctx* ctx, const float* v,
 claire_status claire_transport_noalloc(int nx, int ny, int nz, int nt, const float* v,
                                        const float* m0, float* m1_out, void* stream,
                                        char* err, size_t err_len);
+
+/* ---- batched solves --------------------------------------------------------
+ * Solves npairs independent registrations, each on its own context (its own
+ * grid, images, options), concurrently: up to max_threads host threads
+ * (<= 0: one per pair) each drive one context at a time, and each context
+ * runs on a stream of its own (a private stream is created for contexts on the
+ * legacy default stream), so kernels of different pairs overlap on the GPU.
+ * betas == NULL solves every context at its own beta_v, else nlevels
+ * continuation levels.  v_inout[i] is pair i's device [3][N] initial guess and
+ * result; stats (optional) has npairs entries.  Returns the worst status
+ * (ENOTCONV only when nothing worse happened).  A context must not appear
+ * twice. */
+claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* betas,
+                                 int nlevels, float** v_inout, claire_stats* stats,
+                                 int max_threads);
+
+/* ---- autotuner -------------------------------------------------------------
+ * Times the compiled tile shapes of the SL gather (brick depth along x1: 4, 8
+ * or 16 nodes) and of the FD8 history kernels (8, 16, 32 or 64 planes per
+ * CTA) on this context's grid and buffers and keeps the fastest for all later
+ * calls on the context.  Evaluates J and g at the context's current v first if
+ * nothing has been evaluated yet.  The chosen shapes are returned (NULL ok). */
+claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
 
 /* ---- launch accounting ---------------------------------------------------
  * The context counts every kernel it launches by class, with the algorithmic

@@ -11,8 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libclaire.so")
-SOURCES = ["kernels.cu", "claire_api.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "internal.h", "sl_brick.cuh", "fd8_march.cuh"]
+SOURCES = ["kernels.cu", "mixed.cu", "claire_api.cu", "noalloc.cu"]
+HEADERS = ["common.cuh", "internal.h", "sl_brick.cuh", "fd8_march.cuh", "reduce.cuh"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

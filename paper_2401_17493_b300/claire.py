@@ -24,7 +24,7 @@ EXPORTED = [
     "claire_solve_continuation", "claire_solve_host", "claire_destroy", "claire_last_error",
     "claire_trace", "claire_interp", "claire_grad8", "claire_div8", "claire_spectral",
     "claire_det_deformation_gradient", "claire_profile_reset", "claire_profile_read",
-    "claire_transport_noalloc",
+    "claire_transport_noalloc", "claire_autotune", "claire_solve_batch",
 ]
 
 
@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("max_newton", ctypes.c_int), ("max_pcg", ctypes.c_int),
                 ("fixed_iters", ctypes.c_int), ("forcing", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("verbose", ctypes.c_int),
-                ("gnorm0", ctypes.c_double)]
+                ("gnorm0", ctypes.c_double), ("autotune", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -102,6 +103,9 @@ def load_library(path=LIB_PATH):
         "claire_profile_reset": ([P, I], I),
         "claire_profile_read": ([P, ctypes.POINTER(KernelStat), I], I),
         "claire_transport_noalloc": ([I, I, I, I, P, P, P, P, ctypes.c_char_p, S], I),
+        "claire_autotune": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "claire_solve_batch": ([ctypes.POINTER(P), I, ctypes.POINTER(D), I,
+                                ctypes.POINTER(P), ctypes.POINTER(Stats), I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -123,6 +127,30 @@ def _ptr(t, shape=None, what="array"):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def solve_batch(contexts, vs=None, betas=None, max_threads=0):
+    """Solve independent pairs concurrently (claire_solve_batch).
+
+    contexts: list of Context (images set); vs: list of CUDA (3, n1, n2, n3)
+    initial guesses (None: zeros); betas: continuation levels or None.
+    Returns (vs, [Stats]) and raises on an error status other than
+    ENOTCONV / ELINESEARCH."""
+    import torch
+    L = load_library()
+    n = len(contexts)
+    if vs is None:
+        vs = [torch.zeros(c.vshape, device="cuda") for c in contexts]
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in contexts])
+    ps = (ctypes.c_void_p * n)(*[_ptr(v, c.vshape, "v").value for v, c in zip(vs, contexts)])
+    stats = (Stats * n)()
+    arr = None if betas is None else (ctypes.c_double * len(betas))(*map(float, betas))
+    st = L.claire_solve_batch(hs, n, arr, 0 if betas is None else len(betas), ps, stats,
+                              int(max_threads))
+    if st not in (OK, ENOTCONV, ELINESEARCH):
+        raise ClaireError(st, "claire_solve_batch failed: " + "; ".join(
+            c.lib.claire_last_error(c.h).decode() for c in contexts))
+    return vs, list(stats)
 
 
 NOALLOC_MAX_VOXELS = 1 << 20
@@ -318,6 +346,12 @@ class Context:
         self._check(self.lib.claire_det_deformation_gradient(
             self.h, _ptr(v, self.vshape, "v"), mmm, _ptr(det) if det is not None else None))
         return (mmm[0], mmm[1], mmm[2]), det
+
+    def autotune(self):
+        """Pick the fastest tile shapes for this grid; returns (sl_t1, march_t1)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.claire_autotune(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     # -- launch accounting
     def profile_reset(self, timing=False):

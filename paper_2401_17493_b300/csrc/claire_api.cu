@@ -9,7 +9,9 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -40,6 +42,10 @@ struct claire_ctx {
   int* dflag = nullptr;         // device flag: negative curvature / non-finite PCG scalar
   double* hslots = nullptr;     // pinned host mirror of slots + flag
   int partial_blocks = 0;
+  // mixed precision (options.precision = 1): FP16 histories, allocated on first use
+  __half *mh = nullptr, *lh = nullptr, *sh = nullptr, *lth = nullptr, *ph0 = nullptr,
+         *ph1 = nullptr;
+  float sig_m = 1.0f;           // power-of-two image scale of the FP16 state / adjoint
   float *vtrial = nullptr, *dtrial = nullptr;
   cufftComplex* cbuf = nullptr;
   double *partial = nullptr, *dres = nullptr, *hres = nullptr;
@@ -51,9 +57,23 @@ struct claire_ctx {
   std::string err;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   Profiler prof;
+  Tuning tune;                  // tile shapes for this grid (autotuner)
+  bool tuned = false;
+  // captured PCG iteration parts (options.graphs), indexed by
+  // 4 * (departure-point buffer) + 2 * part + slot parity: the line search swaps
+  // the two departure-point buffers, and kernel arguments are fixed at capture
+  cudaGraphExec_t graph_exec[8] = {};
+  long long graph_launches[8][K_COUNT] = {};
+  double graph_bytes[8][K_COUNT] = {};
+  float* dbuf0 = nullptr;       // first of the two departure-point buffers
+  cudaStream_t own = nullptr;   // private stream for graph capture
+  cudaStream_t user = nullptr;  // the stream of the options
+  cudaEvent_t e_in = nullptr;   // orders the private stream after the user's stream
 };
 
 namespace {
+
+void drop_graphs(claire_ctx* c);
 
 claire_status fail(claire_ctx* c, claire_status s, const char* fmt, ...) {
   char buf[512];
@@ -113,8 +133,21 @@ int64_t N_of(const claire_ctx* c) { return c->g.N; }
 // Routes the launch accounting of the kernels to this context for one API call.
 struct Enter {
   Profiler* prev;
-  explicit Enter(claire_ctx* c) : prev(tl_prof) { tl_prof = c ? &c->prof : nullptr; }
-  ~Enter() { tl_prof = prev; }
+  const Tuning* prev_tune;
+  explicit Enter(claire_ctx* c) : prev(tl_prof), prev_tune(tl_tune) {
+    tl_prof = c ? &c->prof : nullptr;
+    tl_tune = c ? &c->tune : nullptr;
+    // with the private (graph) stream, start after the work already queued on
+    // the caller's stream; every call ends with a synchronisation of its stream
+    if (c && c->own && c->st == c->own && c->e_in) {
+      cudaEventRecord(c->e_in, c->user);
+      cudaStreamWaitEvent(c->st, c->e_in, 0);
+    }
+  }
+  ~Enter() {
+    tl_prof = prev;
+    tl_tune = prev_tune;
+  }
 };
 #define ENTER(c) Enter enter_guard_(c)
 
@@ -163,10 +196,52 @@ claire_status project_data_term(claire_ctx* c, float* b) {
 // ---------------------------------------------------------------- PDE solves
 
 float ht_of(const claire_ctx* c) { return 1.0f / (float)c->nt; }
+bool mixed(const claire_ctx* c) { return c->opt.precision == 1; }
+
+// Slots of the device-side FP64 scalars.
+enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4, SLOT_VMAX = 8 };
+
+// Power-of-two scale that maps max(|m0|, |m1|) into (1/2, 1] (FP16 state range).
+claire_status image_scale(claire_ctx* c) {
+  double a = 0.0, b = 0.0;
+  TRY(reduce(c, N_of(c), c->m0, nullptr, RED_ABSMAX, &a));
+  TRY(reduce(c, N_of(c), c->m1, nullptr, RED_ABSMAX, &b));
+  const double mx = std::max(a, b);
+  if (!std::isfinite(mx)) return fail(c, CLAIRE_ENONFINITE, "images are not finite");
+  int e = 0;
+  if (mx > 0.0) std::frexp(mx, &e);
+  e = std::min(120, std::max(-120, e));
+  c->sig_m = std::ldexp(1.0f, -e);
+  return CLAIRE_OK;
+}
+
+// sum_j w_j lam^j grad m^j (+ base_coef base) into out, FP32 or FP16 histories;
+// with vmax the incremental scale 2^-ceil(log2 *vmax) is undone; with partial,
+// per-block shares of <dotv, out> (PCG curvature).
+claire_status accumulate(claire_ctx* c, const float* lhist, const __half* lh, const float* base,
+                         float base_coef, float* out, const double* vmax, const float* dotv,
+                         double* partial) {
+  if (mixed(c)) {
+    const float umul = 1.0f / (c->sig_m * c->sig_m);
+    if (!launch_accum_hist_h(c->g, lh, c->mh, c->nt, vmax, umul, base, base_coef, out, dotv,
+                             partial, c->st))
+      return fail(c, CLAIRE_EINVAL, "mixed precision needs nt in {1, 2, 4, 8}");
+  } else {
+    launch_accum_hist(c->g, lhist, c->mhist, c->nt, base, base_coef, out, c->st, dotv, partial);
+  }
+  return check_launch(c, "accumulate");
+}
 
 // m^0 = m0, m^{j+1}(x) = m^j(x + d_f(x))  (eq. transport, homogeneous SL steps)
 claire_status state_solve(claire_ctx* c, const float* d) {
   const int64_t N = N_of(c);
+  if (mixed(c)) {                                  // FP16 history of sig_m m
+    launch_axpy_h(N, c->sig_m, c->m0, 0.0f, nullptr, c->mh, c->st);
+    for (int j = 0; j < c->nt; ++j)
+      launch_sl_h(c->g, c->mh + j * N, d, nullptr, 1.0f, nullptr, 0.0f, c->mh + (j + 1) * N,
+                  c->st);
+    return check_launch(c, "state_solve");
+  }
   CUDA_TRY(c, cudaMemcpyAsync(c->mhist, c->m0, N * sizeof(float), cudaMemcpyDeviceToDevice,
                               c->st));
   for (int j = 0; j < c->nt; ++j)
@@ -180,7 +255,17 @@ claire_status objective(claire_ctx* c, const float* v, double* J) {
   const int64_t N = N_of(c);
   const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
   double sq = 0.0, vLv = 0.0;
-  TRY(reduce(c, N, c->mhist + c->nt * N, c->m1, RED_SQDIFF, &sq));
+  if (mixed(c)) {
+    launch_sqdiff_h(N, c->mh + c->nt * N, 1.0f / c->sig_m, c->m1, c->partial, c->red_blocks,
+                    c->dres, c->st);
+    TRY(check_launch(c, "objective"));
+    CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double), cudaMemcpyDeviceToHost,
+                                c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    sq = c->hres[0];
+  } else {
+    TRY(reduce(c, N, c->mhist + c->nt * N, c->m1, RED_SQDIFF, &sq));
+  }
   TRY(spectral(c, CLAIRE_OP_L, v, c->Lv, 1.0));
   TRY(dot3(c, v, c->Lv, &vLv));
   c->dist = 0.5 * h3 * sq;
@@ -197,17 +282,25 @@ claire_status adjoint_and_gradient(claire_ctx* c) {
   launch_trace(g, c->v, nullptr, c->db, ht_of(c), c->st);
   launch_div8(g, c->v, c->D, c->st);
   launch_adjoint_factor(g, c->D, c->db, ht_of(c), c->cf, c->st);
-  launch_lincomb(N, 1.0f, c->m1, -1.0f, c->mhist + c->nt * N, c->lhist + c->nt * N, c->st);
-  for (int j = c->nt - 1; j >= 0; --j)
-    launch_sl(g, c->lhist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lhist + j * N,
-              c->st);
+  if (mixed(c)) {                                  // FP16 history of sig_m lam
+    launch_axpy_h(N, c->sig_m, c->m1, -1.0f, c->mh + c->nt * N, c->lh + c->nt * N, c->st);
+    for (int j = c->nt - 1; j >= 0; --j)
+      launch_sl_h(g, c->lh + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lh + j * N,
+                  c->st);
+  } else {
+    launch_lincomb(N, 1.0f, c->m1, -1.0f, c->mhist + c->nt * N, c->lhist + c->nt * N, c->st);
+    for (int j = c->nt - 1; j >= 0; --j)
+      launch_sl(g, c->lhist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lhist + j * N,
+                c->st);
+  }
   TRY(check_launch(c, "adjoint"));
   if (c->opt.beta_w > 0.0) {
-    launch_accum_hist(g, c->lhist, c->mhist, c->nt, nullptr, 0.0f, c->grad, c->st);
+    TRY(accumulate(c, c->lhist, c->lh, nullptr, 0.0f, c->grad, nullptr, nullptr, nullptr));
     TRY(project_data_term(c, c->grad));
     launch_axpby(3 * N, (float)c->beta_v, c->Lv, 1.0f, c->grad, c->st);
   } else {
-    launch_accum_hist(g, c->lhist, c->mhist, c->nt, c->Lv, (float)c->beta_v, c->grad, c->st);
+    TRY(accumulate(c, c->lhist, c->lh, c->Lv, (float)c->beta_v, c->grad, nullptr, nullptr,
+                   nullptr));
   }
   return check_launch(c, "gradient");
 }
@@ -236,15 +329,23 @@ claire_status matvec(claire_ctx* c, const float* vt, float* Hvt) {
     return fail(c, CLAIRE_EORDER, "hessian_matvec needs a prior objective_gradient");
   const int64_t N = N_of(c);
   const Grid& g = c->g;
+  (void)g;
+  const double* vmax = nullptr;
+  if (mixed(c)) {                                  // scale of the FP16 incremental fields
+    launch_reduce(3 * N, vt, nullptr, RED_ABSMAX, c->partial, c->red_blocks,
+                  c->slots + SLOT_VMAX, c->st);
+    vmax = c->slots + SLOT_VMAX;
+  }
   TRY(matvec_transport(c, vt));
   TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
   if (c->opt.beta_w > 0.0) {
-    launch_accum_hist(g, c->lthist, c->mhist, c->nt, nullptr, 0.0f, Hvt, c->st);
+    TRY(accumulate(c, c->lthist, c->lth, nullptr, 0.0f, Hvt, vmax, nullptr, nullptr));
     TRY(project_data_term(c, Hvt));
     TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
     launch_axpby(3 * N, (float)c->beta_v, c->scr3, 1.0f, Hvt, c->st);
   } else {
-    launch_accum_hist(g, c->lthist, c->mhist, c->nt, c->scr3, (float)c->beta_v, Hvt, c->st);
+    TRY(accumulate(c, c->lthist, c->lth, c->scr3, (float)c->beta_v, Hvt, vmax, nullptr,
+                   nullptr));
   }
   return check_launch(c, "matvec accumulate");
 }
@@ -262,6 +363,25 @@ claire_status matvec_transport(claire_ctx* c, const float* vt) {
   const Grid& g = c->g;
   const float ht = ht_of(c);
   const int nt = c->nt;
+  if (mixed(c)) {                // FP16 incremental fields scaled by sig_m 2^-ceil(log2 |vt|)
+    if (!launch_sdot_hist_h(g, c->mh, nt, vt, -0.5f * ht, c->slots + SLOT_VMAX, c->sh, c->st))
+      return fail(c, CLAIRE_EINVAL, "mixed precision needs nt in {1, 2, 4, 8}");
+    const __half* src = c->sh;
+    for (int j = 0; j < nt; ++j) {
+      if (j < nt - 1) {
+        __half* dst = (j % 2 == 0) ? c->ph0 : c->ph1;
+        launch_sl_h(g, src, c->df, nullptr, 1.0f, c->sh + (j + 1) * N, -ht, dst, c->st);
+        src = dst;
+      } else {
+        launch_sl_h(g, src, c->df, nullptr, -1.0f, c->sh + nt * N, 0.5f * ht, c->lth + nt * N,
+                    c->st);
+      }
+    }
+    for (int j = nt - 1; j >= 0; --j)
+      launch_sl_h(g, c->lth + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lth + j * N,
+                  c->st);
+    return check_launch(c, "matvec transport");
+  }
   launch_sdot_hist(g, c->mhist, nt, vt, -0.5f * ht, c->shist, c->st);
   const float* src = c->shist;                       // w^0
   for (int j = 0; j < nt; ++j) {
@@ -279,9 +399,6 @@ claire_status matvec_transport(claire_ctx* c, const float* vt) {
               c->st);
   return check_launch(c, "matvec transport");
 }
-
-// Slots of the device-side PCG scalars.
-enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4 };
 
 // z = M^-1 r with M = beta_v L (zero symbol set to one); <r, z> by Parseval into
 // slots[rz_slot] and the component means of r into slots[SLOT_MEAN..+2].
@@ -308,12 +425,104 @@ claire_status precondition(claire_ctx* c, int rz_slot) {
 // so each iteration costs one FFT pair (the preconditioner) besides the
 // transport solves.  One host synchronisation per iteration reads <s, H s> and
 // ||r||^2 for the curvature and stopping tests.
+// One PCG iteration is two launch sequences around the host check:
+//  part A (slot parity cur): H s (transport solves + accumulation with <s, H s>),
+//          the kappa update of vt and r with ||r||^2, and the copy of the FP64
+//          slots to pinned host memory;
+//  part B (cur -> nxt): z = M^-1 r with <r, z>, the mu update of s and beta_v L s
+//          (and ||s||_inf for the FP16 scale in mixed precision).
+claire_status pcg_part_a(claire_ctx* c, int cur) {
+  const int64_t n3 = 3 * N_of(c);
+  const Grid& g = c->g;
+  const double* vmax = mixed(c) ? c->slots + SLOT_VMAX : nullptr;
+  TRY(matvec_transport(c, c->s));
+  if (c->opt.beta_w <= 0.0 && march_supported(c->nt)) {
+    TRY(accumulate(c, c->lthist, c->lth, c->hs, 1.0f, c->Hs, vmax, c->s, c->partial));
+    launch_reduce_final(c->partial, march_blocks(g), RED_SUM, c->slots + SLOT_SHS, c->st);
+  } else {
+    TRY(accumulate(c, c->lthist, c->lth, nullptr, 0.0f, c->Hs, vmax, nullptr, nullptr));
+    TRY(project_data_term(c, c->Hs));
+    launch_axpby(n3, 1.0f, c->hs, 1.0f, c->Hs, c->st);
+    launch_reduce(n3, c->s, c->Hs, RED_DOT, c->partial, c->red_blocks, c->slots + SLOT_SHS,
+                  c->st);
+  }
+  const int vb = vector_blocks(n3 / 4);
+  launch_pcg_update(n3, c->slots + cur, c->slots + SLOT_SHS, c->vt, c->r, c->s, c->Hs,
+                    c->partial, vb, c->dflag, c->st);
+  launch_reduce_final(c->partial, vb, RED_SUM, c->slots + SLOT_RR, c->st);
+  TRY(check_launch(c, "pcg update"));
+  CUDA_TRY(c, cudaMemcpyAsync(c->hslots, c->slots, 16 * sizeof(double) + sizeof(int),
+                              cudaMemcpyDeviceToHost, c->st));
+  return CLAIRE_OK;
+}
+
+claire_status pcg_part_b(claire_ctx* c, int cur, int nxt) {
+  const int64_t N = N_of(c);
+  TRY(precondition(c, nxt));
+  launch_s_update(N, c->slots + nxt, c->slots + cur, c->slots + SLOT_MEAN, 0, c->z, c->r, c->s,
+                  c->hs, c->st);
+  if (mixed(c))
+    launch_reduce(3 * N, c->s, nullptr, RED_ABSMAX, c->partial, c->red_blocks,
+                  c->slots + SLOT_VMAX, c->st);
+  return check_launch(c, "pcg part b");
+}
+
+void drop_graphs(claire_ctx* c) {
+  for (auto& e : c->graph_exec)
+    if (e) {
+      cudaGraphExecDestroy(e);
+      e = nullptr;
+    }
+}
+
+// Run part A (which = 0) or B (which = 1) for parity p, as a captured CUDA
+// graph when options.graphs is set (captured on first use; the kernels inside
+// are counted per replay, not event-timed).
+claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
+  if (!c->opt.graphs)
+    return which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
+  const int slot = 4 * (c->df == c->dbuf0 ? 0 : 1) + 2 * which + (cur == SLOT_RZ0 ? 0 : 1);
+  if (!c->graph_exec[slot]) {
+    Profiler* saved = tl_prof;
+    Profiler counter;                               // counts the captured launches
+    tl_prof = &counter;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    claire_status s = which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
+    cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+    tl_prof = saved;
+    if (s != CLAIRE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph_exec[slot], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    for (int k = 0; k < K_COUNT; ++k) {
+      c->graph_launches[slot][k] = counter.launches[k];
+      c->graph_bytes[slot][k] = counter.bytes[k];
+    }
+  }
+  if (tl_prof)
+    for (int k = 0; k < K_COUNT; ++k) {
+      tl_prof->launches[k] += c->graph_launches[slot][k];
+      tl_prof->bytes[k] += c->graph_bytes[slot][k];
+    }
+  CUDA_TRY(c, cudaGraphLaunch(c->graph_exec[slot], c->st));
+  return CLAIRE_OK;
+}
+
+// Algorithm 2: PCG for H vt = -g from vt = 0 with M = beta_v L (zero symbol -> 1).
+// The scalars kappa and mu stay on the device (FP64 slots); the regularisation
+// part of H s is carried by the recurrence beta_v L s = (r - mean r) + mu beta_v L s,
+// so each iteration costs one FFT pair (the preconditioner) besides the
+// transport solves.  One host synchronisation per iteration reads <s, H s> and
+// ||r||^2 for the curvature and stopping tests.
 claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
   const int64_t N = N_of(c);
   const int64_t n3 = 3 * N;
-  const Grid& g = c->g;
   *curv = CLAIRE_OK;
-  const int vb = vector_blocks(n3 / 4);
   CUDA_TRY(c, cudaMemsetAsync(c->vt, 0, n3 * sizeof(float), c->st));
   CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
   launch_lincomb(n3, -1.0f, c->grad, 0.0f, c->grad, c->r, c->st);    // r = -g
@@ -321,28 +530,14 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
   TRY(precondition(c, cur));
   launch_s_update(N, c->slots + cur, c->slots + cur, c->slots + SLOT_MEAN, 1, c->z, c->r, c->s,
                   c->hs, c->st);
-  const bool fused = c->opt.beta_w <= 0.0 && march_supported(c->nt);
+  if (mixed(c))
+    launch_reduce(n3, c->s, nullptr, RED_ABSMAX, c->partial, c->red_blocks,
+                  c->slots + SLOT_VMAX, c->st);
   for (int it = 1; it <= c->opt.max_pcg; ++it) {
-    TRY(matvec_transport(c, c->s));
-    if (fused) {
-      launch_accum_hist(g, c->lthist, c->mhist, c->nt, c->hs, 1.0f, c->Hs, c->st, c->s,
-                        c->partial);
-      launch_reduce_final(c->partial, march_blocks(g), RED_SUM, c->slots + SLOT_SHS, c->st);
-    } else {
-      launch_accum_hist(g, c->lthist, c->mhist, c->nt, nullptr, 0.0f, c->Hs, c->st);
-      TRY(project_data_term(c, c->Hs));
-      launch_axpby(n3, 1.0f, c->hs, 1.0f, c->Hs, c->st);
-      launch_reduce(n3, c->s, c->Hs, RED_DOT, c->partial, c->red_blocks, c->slots + SLOT_SHS,
-                    c->st);
-    }
+    const int nxt = cur == SLOT_RZ0 ? SLOT_RZ1 : SLOT_RZ0;
+    TRY(pcg_part(c, 0, cur, nxt));
     ++k.matvecs;
     k.pde += 2;
-    launch_pcg_update(n3, c->slots + cur, c->slots + SLOT_SHS, c->vt, c->r, c->s, c->Hs,
-                      c->partial, vb, c->dflag, c->st);
-    launch_reduce_final(c->partial, vb, RED_SUM, c->slots + SLOT_RR, c->st);
-    TRY(check_launch(c, "pcg update"));
-    CUDA_TRY(c, cudaMemcpyAsync(c->hslots, c->slots, 16 * sizeof(double) + sizeof(int),
-                                cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     const double sHs = c->hslots[SLOT_SHS], rr = c->hslots[SLOT_RR];
     const int flag = *(const int*)(c->hslots + 16);
@@ -358,12 +553,8 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
     ++k.pcg;
     if (!c->opt.fixed_iters && std::sqrt(rr) < tol) break;
     if (it == c->opt.max_pcg) break;
-    const int nxt = cur == SLOT_RZ0 ? SLOT_RZ1 : SLOT_RZ0;
-    TRY(precondition(c, nxt));
-    launch_s_update(N, c->slots + nxt, c->slots + cur, c->slots + SLOT_MEAN, 0, c->z, c->r,
-                    c->s, c->hs, c->st);
+    TRY(pcg_part(c, 1, cur, nxt));
     cur = nxt;
-    TRY(check_launch(c, "pcg"));
   }
   return check_launch(c, "pcg");
 }
@@ -408,6 +599,57 @@ claire_status absmax3(claire_ctx* c, const float* a, double* out) {
   return reduce(c, 3 * N_of(c), a, nullptr, RED_ABSMAX, out);
 }
 
+// Autotuner: time each compiled tile shape on this context's own grid and
+// buffers (the state history and departure points of the current evaluation)
+// with CUDA events, keep the fastest.  Brick depth along x1 for the SL steps
+// (4, 8, 16), planes per CTA for the FD8 history kernels (8, 16, 32, 64).
+claire_status autotune(claire_ctx* c) {
+  if (!c->have_eval) return fail(c, CLAIRE_EORDER, "autotune needs an evaluated state");
+  const int64_t N = N_of(c);
+  cudaEvent_t a = c->e0, b = c->e1;
+  auto time_it = [&](auto&& fn, float* ms) -> claire_status {
+    fn();                                           // warm-up (and attribute setup)
+    CUDA_TRY(c, cudaEventRecord(a, c->st));
+    for (int r = 0; r < 3; ++r) fn();
+    CUDA_TRY(c, cudaEventRecord(b, c->st));
+    CUDA_TRY(c, cudaEventSynchronize(b));
+    CUDA_TRY(c, cudaEventElapsedTime(ms, a, b));
+    return check_launch(c, "autotune");
+  };
+  Profiler* saved = tl_prof;
+  tl_prof = nullptr;                                // tuning launches are not counted
+  float best = 1e30f;
+  Tuning t = c->tune;
+  for (int t1 : {4, 8, 16}) {
+    c->tune.sl_t1 = t1;
+    float ms = 0.f;
+    claire_status s = mixed(c)
+        ? time_it([&] { launch_sl_h(c->g, c->mh, c->df, nullptr, 1.f, nullptr, 0.f, c->ph0,
+                                    c->st); }, &ms)
+        : time_it([&] { launch_sl(c->g, c->mhist, c->df, nullptr, 1.f, nullptr, 0.f, c->pp0,
+                                  c->st); }, &ms);
+    if (s != CLAIRE_OK) { tl_prof = saved; return s; }
+    if (ms < best) { best = ms; t.sl_t1 = t1; }
+  }
+  c->tune.sl_t1 = t.sl_t1;
+  best = 1e30f;
+  if (march_supported(c->nt)) {
+    for (int m1 : {8, 16, 32, 64}) {
+      c->tune.march_t1 = m1;
+      float ms = 0.f;
+      claire_status s = time_it([&] { (void)accumulate(c, c->lhist, c->lh, c->Lv, 1.0f, c->scr3,
+                                                       nullptr, nullptr, nullptr); }, &ms);
+      if (s != CLAIRE_OK) { tl_prof = saved; return s; }
+      if (ms < best) { best = ms; t.march_t1 = m1; }
+    }
+  }
+  c->tune = t;
+  c->tuned = true;
+  tl_prof = saved;
+  (void)N;
+  return CLAIRE_OK;
+}
+
 // Algorithm 1 from the iterate in c->v; gnorm0 > 0 fixes the relative-gradient
 // denominator (reading C-10), else ||g(v = 0)||_inf is computed first.
 claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_stats* out) {
@@ -426,6 +668,7 @@ claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_sta
   }
   TRY(evaluate(c));
   k.pde += 2;
+  if (c->opt.autotune && !c->tuned) TRY(autotune(c));
   double gn = 0.0;
   TRY(absmax3(c, c->grad, &gn));
   if (!std::isfinite(gn)) return fail(c, CLAIRE_ENONFINITE, "gradient is not finite");
@@ -516,12 +759,16 @@ claire_status claire_default_options(claire_options* o) {
   o->stream = nullptr;
   o->verbose = 0;
   o->gnorm0 = 0.0;
+  o->autotune = 0;
+  o->graphs = 0;
   return CLAIRE_OK;
 }
 
 claire_status claire_destroy(claire_ctx* c) {
   if (!c) return CLAIRE_OK;
   c->prof.release();
+  drop_graphs(c);
+  if (c->own) cudaStreamDestroy(c->own);
   if (c->plans) {
     cufftDestroy(c->r2c);
     cufftDestroy(c->c2r);
@@ -532,6 +779,7 @@ claire_status claire_destroy(claire_ctx* c) {
   if (c->hslots) cudaFreeHost(c->hslots);
   if (c->e0) cudaEventDestroy(c->e0);
   if (c->e1) cudaEventDestroy(c->e1);
+  if (c->e_in) cudaEventDestroy(c->e_in);
   delete c;
   return CLAIRE_OK;
 }
@@ -560,6 +808,7 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
                        &c->z, &c->s, &c->Hs, &c->hs, &c->vtrial, &c->dtrial};
   for (auto p : fields1) if (s == CLAIRE_OK) s = alloc(c, p, N);
   for (auto p : fields3) if (s == CLAIRE_OK) s = alloc(c, p, 3 * N);
+  c->dbuf0 = c->df;
   float** hists[] = {&c->mhist, &c->lhist, &c->shist, &c->lthist};
   for (auto p : hists) if (s == CLAIRE_OK) s = alloc(c, p, (int64_t)(nt + 1) * N);
   const int64_t Nc = (int64_t)nx * ny * (nz / 2 + 1);
@@ -602,7 +851,9 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
       c->plans = true;
   }
   if (s == CLAIRE_OK && (cudaEventCreate(&c->e0) != cudaSuccess ||
-                         cudaEventCreate(&c->e1) != cudaSuccess))
+                         cudaEventCreate(&c->e1) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&c->e_in, cudaEventDisableTiming) !=
+                             cudaSuccess))
     s = CLAIRE_ECUDA;
   if (s == CLAIRE_OK) {
     cudaMemset(c->m0, 0, N * sizeof(float));
@@ -626,10 +877,29 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
     return fail(c, CLAIRE_EINVAL, "invalid option value");
   if (o->hessian == 1)
     return fail(c, CLAIRE_EINVAL, "full-Newton Hessian is not available in this build");
-  if (o->precision == 1)
-    return fail(c, CLAIRE_EINVAL, "mixed precision is not available in this build");
+  if (o->precision == 1 && !march_supported(c->nt))
+    return fail(c, CLAIRE_EINVAL, "mixed precision needs nt in {1, 2, 4, 8}");
+  if (o->precision == 1 && c->mh == nullptr) {   // FP16 histories on first use
+    const int64_t N = N_of(c);
+    const int64_t nh = 4 * (int64_t)(c->nt + 1) * N + 2 * N;
+    float* p = nullptr;
+    TRY(alloc(c, &p, (nh + 1) / 2));
+    __half* h = reinterpret_cast<__half*>(p);
+    c->mh = h;
+    c->lh = h + (c->nt + 1) * N;
+    c->sh = h + 2 * (c->nt + 1) * N;
+    c->lth = h + 3 * (c->nt + 1) * N;
+    c->ph0 = h + 4 * (c->nt + 1) * N;
+    c->ph1 = c->ph0 + N;
+  }
+  drop_graphs(c);
   c->opt = *o;
-  c->st = (cudaStream_t)o->stream;
+  c->user = (cudaStream_t)o->stream;
+  if (o->graphs && c->own == nullptr)
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+  // graphs are captured on the private stream (the legacy default stream
+  // cannot be captured); calls order it after / before the user's stream
+  c->st = o->graphs ? c->own : c->user;
   CUFFT_TRY(c, cufftSetStream(c->r2c, c->st));
   CUFFT_TRY(c, cufftSetStream(c->c2r, c->st));
   c->have_eval = false;
@@ -644,6 +914,7 @@ claire_status claire_get_options(const claire_ctx* c, claire_options* o) {
 
 claire_status claire_set_beta(claire_ctx* c, double beta_v) {
   if (!c || !(beta_v > 0.0)) return CLAIRE_EINVAL;
+  if (beta_v != c->beta_v) drop_graphs(c);
   c->beta_v = beta_v;
   c->have_eval = false;
   return CLAIRE_OK;
@@ -661,7 +932,7 @@ claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1)
   CUDA_TRY(c, cudaMemcpyAsync(c->m1, m1, b, cudaMemcpyDeviceToDevice, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   c->have_eval = false;
-  return CLAIRE_OK;
+  return image_scale(c);
 }
 
 claire_status claire_transport(claire_ctx* c, const float* v, float* m1_out) {
@@ -715,11 +986,16 @@ static claire_status solve_levels(claire_ctx* c, const double* betas, int nlev, 
   memset(out, 0, sizeof *out);
   Counters k;
   const size_t b3 = 3 * N_of(c) * sizeof(float);
+  if (c->st != c->user) {                          // private stream: start after the user's work
+    CUDA_TRY(c, cudaEventRecord(c->e1, c->user));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->e1, 0));
+  }
   CUDA_TRY(c, cudaEventRecord(c->e0, c->st));
   if (v_in) CUDA_TRY(c, cudaMemcpyAsync(c->v, v_in, b3, cudaMemcpyDeviceToDevice, c->st));
   double gnorm0 = c->opt.gnorm0;
   claire_status s = CLAIRE_OK;
   for (int i = 0; i < nlev; ++i) {
+    if (betas[i] != c->beta_v) drop_graphs(c);
     c->beta_v = betas[i];
     s = gauss_newton(c, gnorm0, k, out);
     gnorm0 = out->gnorm0;
@@ -729,6 +1005,7 @@ static claire_status solve_levels(claire_ctx* c, const double* betas, int nlev, 
   if (v_out) e = cudaMemcpyAsync(v_out, c->v, b3, cudaMemcpyDeviceToDevice, c->st);
   if (e == cudaSuccess) e = cudaEventRecord(c->e1, c->st);
   if (e == cudaSuccess) e = cudaEventSynchronize(c->e1);
+  if (e == cudaSuccess && c->st != c->user) e = cudaStreamWaitEvent(c->user, c->e1, 0);
   if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "solve epilogue: %s", cudaGetErrorString(e));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->e0, c->e1);
@@ -758,6 +1035,7 @@ claire_status claire_solve_host(claire_ctx* c, const float* m0_host, const float
   CUDA_TRY(c, cudaMemcpyAsync(c->m1, m1_host, b, cudaMemcpyHostToDevice, c->st));
   CUDA_TRY(c, cudaMemcpyAsync(c->v, v_inout_host, 3 * b, cudaMemcpyHostToDevice, c->st));
   c->have_eval = false;
+  TRY(image_scale(c));
   const double beta = c->beta_v;
   claire_status s = betas ? solve_levels(c, betas, nlevels, nullptr, nullptr, st)
                           : solve_levels(c, &beta, 1, nullptr, nullptr, st);
@@ -845,6 +1123,75 @@ claire_status claire_det_deformation_gradient(claire_ctx* c, const float* v, dou
   if (det_out) CUDA_TRY(c, cudaMemcpyAsync(det_out, det, N * sizeof(float),
                                            cudaMemcpyDeviceToDevice, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* betas,
+                                int nlevels, float** v_inout, claire_stats* stats,
+                                int max_threads) {
+  if (!ctxs || npairs < 1 || !v_inout || (betas && nlevels < 1)) return CLAIRE_EINVAL;
+  for (int i = 0; i < npairs; ++i) {
+    if (!ctxs[i] || !v_inout[i]) return CLAIRE_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], CLAIRE_EINVAL, "context given twice");
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CLAIRE_ECUDA;
+  // every pair runs on a stream of its own so that the pairs overlap on the GPU
+  std::vector<cudaStream_t> saved(npairs);
+  for (int i = 0; i < npairs; ++i) {
+    claire_ctx* c = ctxs[i];
+    saved[i] = c->st;
+    if (c->st == nullptr) {
+      if (c->own == nullptr)
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+      c->st = c->own;
+      CUFFT_TRY(c, cufftSetStream(c->r2c, c->st));
+      CUFFT_TRY(c, cufftSetStream(c->c2r, c->st));
+    }
+  }
+  std::vector<claire_status> res(npairs, CLAIRE_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next++; i < npairs; i = next++) {
+      claire_ctx* c = ctxs[i];
+      const double b = c->beta_v;
+      res[i] = betas ? solve_levels(c, betas, nlevels, v_inout[i], v_inout[i],
+                                    stats ? stats + i : nullptr)
+                     : solve_levels(c, &b, 1, v_inout[i], v_inout[i],
+                                    stats ? stats + i : nullptr);
+    }
+  };
+  const int nt = std::max(1, std::min(npairs, max_threads > 0 ? max_threads : npairs));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < npairs; ++i) {
+    claire_ctx* c = ctxs[i];
+    if (c->st != saved[i]) {
+      cudaStreamSynchronize(c->st);
+      c->st = saved[i];
+      cufftSetStream(c->r2c, c->st);
+      cufftSetStream(c->c2r, c->st);
+    }
+  }
+  claire_status worst = CLAIRE_OK;
+  for (int i = 0; i < npairs; ++i)
+    if (res[i] != CLAIRE_OK && res[i] != CLAIRE_ENOTCONV) worst = res[i];
+  if (worst == CLAIRE_OK)
+    for (int i = 0; i < npairs; ++i)
+      if (res[i] != CLAIRE_OK) worst = res[i];
+  return worst;
+}
+
+claire_status claire_autotune(claire_ctx* c, int* sl_t1, int* march_t1) {
+  if (!c) return CLAIRE_EINVAL;
+  ENTER(c);
+  if (!c->have_eval) TRY(evaluate(c));
+  TRY(autotune(c));
+  if (sl_t1) *sl_t1 = c->tune.sl_t1;
+  if (march_t1) *march_t1 = c->tune.march_t1;
   return CLAIRE_OK;
 }
 

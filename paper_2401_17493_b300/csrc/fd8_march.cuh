@@ -14,17 +14,16 @@
 #pragma once
 
 #include "common.cuh"
+#include "reduce.cuh"
 
 namespace claire {
 
-__device__ __forceinline__ double block_sum(double v);
-
-constexpr int MT2 = 8, MT3 = 32, MT1 = 32;          // tile x2, x3; planes per CTA
+constexpr int MT2 = 8, MT3 = 32, MT1 = 32;          // tile x2, x3; default planes per CTA
 constexpr int MP2 = MT2 + 8, MP3 = MT3 + 8;         // staged plane with the FD8 halo
 constexpr int MPLANE = MP2 * MP3;                   // 640 floats
 
-__host__ inline dim3 march_grid(const Grid& g) {
-  return dim3((g.n3 + MT3 - 1) / MT3, (g.n2 + MT2 - 1) / MT2, (g.n1 + MT1 - 1) / MT1);
+__host__ inline dim3 march_grid(const Grid& g, int mt1 = MT1) {
+  return dim3((g.n3 + MT3 - 1) / MT3, (g.n2 + MT2 - 1) / MT2, (g.n1 + mt1 - 1) / mt1);
 }
 
 __device__ __forceinline__ void stage_plane(const float* __restrict__ u, const Grid& g, int i1,
@@ -58,10 +57,11 @@ __global__ void __launch_bounds__(32 * MT2) k_hist_march(Grid g, const float* __
                                                          float base_coef,
                                                          float* __restrict__ out,
                                                          const float* __restrict__ dotv,
-                                                         double* __restrict__ partial) {
+                                                         double* __restrict__ partial,
+                                                         int mt1) {
   __shared__ __align__(16) float sp[NF][MPLANE];
   const int lane = threadIdx.x, ty = threadIdx.y;
-  const int i3_0 = blockIdx.x * MT3, i2_0 = blockIdx.y * MT2, i1_0 = blockIdx.z * MT1;
+  const int i3_0 = blockIdx.x * MT3, i2_0 = blockIdx.y * MT2, i1_0 = blockIdx.z * mt1;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   const bool active = i2 < g.n2 && i3 < g.n3;
   const int64_t N = g.N;
@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(32 * MT2) k_hist_march(Grid g, const float* __
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       q[f][k] = active ? __ldg(mhist + f * N + wrap_any(i1_0 - 4 + k, g.n1) * s1 + col) : 0.f;
-  const int i1_end = min(i1_0 + MT1, g.n1);
-  double dacc = 0.0;
+  const int i1_end = min(i1_0 + mt1, g.n1);
+  KahanF dacc;
   const int c = (ty + 4) * MP3 + lane + 4;                     // node in the staged plane
   for (int i1 = i1_0; i1 < i1_end; ++i1) {
     // queue head m(i1 + 4)
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(32 * MT2) k_hist_march(Grid g, const float* __
         out[N + idx] = a1;
         out[2 * N + idx] = a2;
         if (partial)
-          dacc += (double)(dotv[idx] * a0 + dotv[N + idx] * a1 + dotv[2 * N + idx] * a2);
+          dacc.add(dotv[idx] * a0 + dotv[N + idx] * a1 + dotv[2 * N + idx] * a2);
       }
     }
     // advance the queues
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(32 * MT2) k_hist_march(Grid g, const float* __
       for (int k = 0; k < 8; ++k) q[f][k] = q[f][k + 1];
   }
   if (MODE == 1 && partial) {
-    const double b = block_sum(dacc);
+    const double b = block_sum(dacc.value());
     if (threadIdx.x == 0 && threadIdx.y == 0)
       partial[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
   }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the kernel launchers and the host solver.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cufft.h>
 #include <cuda_runtime.h>
 
@@ -39,6 +40,16 @@ struct Profiler {
 
 // The profiler of the context whose API call is running on this thread.
 extern thread_local Profiler* tl_prof;
+
+// Tile shapes picked by the autotuner for one grid: x1 depth of the SL brick
+// (4, 8 or 16 nodes) and planes per CTA of the FD8 march (8, 16, 32 or 64).
+struct Tuning {
+  int sl_t1 = 8;
+  int march_t1 = 32;
+};
+extern thread_local const Tuning* tl_tune;
+int tuned_sl_t1();
+int tuned_march_t1();
 
 struct ProfileRange {
   int kind;
@@ -86,6 +97,19 @@ void launch_lincomb(int64_t n, float a, const float* x, float b, const float* y,
                     cudaStream_t st);
 void launch_detf(const Grid& g, const float* v, const float* df, int nt, float* F, float* Fn,
                  float* A, float* Ay, float* det, cudaStream_t st);
+
+// Mixed-precision (FP16 storage) launchers, see mixed.cu.
+void launch_sl_h(const Grid& g, const __half* u, const float* d, const float* scale,
+                 float sigma, const __half* aux, float beta, __half* out, cudaStream_t st);
+bool launch_sdot_hist_h(const Grid& g, const __half* mhist, int nt, const float* vt,
+                        float scale0, const double* vmax, __half* shist, cudaStream_t st);
+bool launch_accum_hist_h(const Grid& g, const __half* lhist, const __half* mhist, int nt,
+                         const double* vmax, float umul, const float* base, float base_coef,
+                         float* out, const float* dotv, double* partial, cudaStream_t st);
+void launch_axpy_h(int64_t n, float a, const float* x, float b, const __half* z, __half* y,
+                   cudaStream_t st);
+void launch_sqdiff_h(int64_t n, const __half* m, float a, const float* m1, double* partial,
+                     int nblocks, double* out, cudaStream_t st);
 
 enum ReduceMode {
   RED_DOT = 0, RED_SQDIFF = 1, RED_ABSMAX = 2, RED_SQ = 3, RED_MAX = 4, RED_MIN = 5, RED_SUM = 6

@@ -15,7 +15,11 @@
 // for the L1 reuse of the 64-tap gathers).
 #include <math_constants.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "internal.h"
+#include "reduce.cuh"
 #include "sl_brick.cuh"
 #include "fd8_march.cuh"
 
@@ -41,14 +45,15 @@ static dim3 grid3(const Grid& g) {
 // y = x -+ (h_t / 2)(v(x) + v(y~)) is stored as y - x in grid units.
 __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __restrict__ v,
                                                          float* __restrict__ df,
-                                                         float* __restrict__ db, float ht) {
+                                                         float* __restrict__ db, float ht,
+                                                         int t1) {
   extern __shared__ __align__(16) float sm[];
-  const int i1_0 = blockIdx.z * TB1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+  const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
   const int64_t N = g.N;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   const bool active = i2 < g.n2 && i3 < g.n3;
-  const int kmax = min(TB1, g.n1 - i1_0);
+  const int kmax = min(t1, g.n1 - i1_0);
   bool first = true;
 #pragma unroll 1
   for (int dir = 0; dir < 2; ++dir) {
@@ -59,7 +64,7 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __
     for (int c = 0; c < 3; ++c) {
       if (!first) __syncthreads();               // previous brick consumed
       first = false;
-      stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm);
+      stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm, t1);
       __syncthreads();
       if (!active) continue;
       const float ihc = c == 0 ? g.inv_h1 : (c == 1 ? g.inv_h2 : g.inv_h3);
@@ -91,20 +96,21 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl(Grid g, const float* __res
                                                       const float* __restrict__ scale,
                                                       float sigma,
                                                       const float* __restrict__ aux, float beta,
-                                                      float ht, float* __restrict__ out) {
+                                                      float ht, float* __restrict__ out,
+                                                      int t1) {
   extern __shared__ __align__(16) float sm[];
-  const int i1_0 = blockIdx.z * TB1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
-  stage_brick(u, g, i1_0, i2_0, i3_0, sm);
+  const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+  stage_brick(u, g, i1_0, i2_0, i3_0, sm, t1);
   __syncthreads();
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   if (i2 >= g.n2 || i3 >= g.n3) return;
   const int64_t N = g.N;
   const int ctr = (HB_LO * BB2 + ty + HB_LO) * BB3 + lane + HB3_LO;
+  const int kmax = min(t1, g.n1 - i1_0);
 #pragma unroll 2
-  for (int k = 0; k < TB1; ++k) {
+  for (int k = 0; k < kmax; ++k) {
     const int i1 = i1_0 + k;
-    if (i1 >= g.n1) break;
     const int64_t idx = lin(g, i1, i2, i3);
     NodeTaps t;
     node_taps(d[idx], d[N + idx], d[2 * N + idx], t);
@@ -220,9 +226,6 @@ __global__ void __launch_bounds__(256) k_accum_hist(Grid g, const float* __restr
 
 // Half spectrum [n1][n2][n3/2+1] of 3 components (stride Nc).  Integer
 // wavenumbers k_i in FFT order; scale folds in cuFFT's 1/N.
-// Reduction helpers (defined below with the reductions).
-__device__ __forceinline__ double block_sum(double v);
-
 // Optional fused outputs: partial[blockIdx.x] = this block's share of the real
 // inner product <in, out> by Parseval over the half spectrum (weight 2 for the
 // modes whose conjugates are not stored); means[0..2] = the k = 0 coefficient
@@ -302,54 +305,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-// max that keeps a NaN (fmax would drop it): the infinity norm must expose non-finite fields
-__device__ __forceinline__ double nanmax(double a, double b) {
-  return a != a ? a : (b != b ? b : fmax(a, b));
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ double nanmin(double a, double b) {
-  return a != a ? a : (b != b ? b : fmin(a, b));
-}
-
-// Reduction modes (ReduceMode): 0 sum a b, 1 sum (a - b)^2, 2 max |a|, 3 sum a^2,
-// 4 max a, 5 min a, 6 sum a.  Max / min keep NaNs so non-finite fields show.
-__device__ __forceinline__ bool red_is_max(int mode) { return mode == 2 || mode == 4; }
-__device__ __forceinline__ double red_init(int mode) {
-  return mode == 4 ? -CUDART_INF : (mode == 5 ? CUDART_INF : 0.0);
-}
-__device__ __forceinline__ double red_combine(int mode, double a, double b) {
-  return red_is_max(mode) ? nanmax(a, b) : (mode == 5 ? nanmin(a, b) : a + b);
-}
-__device__ __forceinline__ double warp_red(int mode, double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = red_combine(mode, v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Block-wide reduction; the result is valid in thread (0, 0).  Works for 1D
-// and 2D blocks (linear thread id); call once per kernel by every thread.
-__device__ __forceinline__ double block_red(int mode, double acc) {
-  __shared__ double sh[32];
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
-  acc = warp_red(mode, acc);
-  if ((tid & 31) == 0) sh[tid >> 5] = acc;
-  __syncthreads();
-  double v = red_init(mode);
-  if (tid < 32) {
-    v = tid < nwarps ? sh[tid] : red_init(mode);
-    v = warp_red(mode, v);
-  }
-  return v;
-}
-
-__device__ __forceinline__ double block_sum(double v) { return block_red(0, v); }
-
 // Each thread folds 4 elements (one float4 per operand) in FP32, then adds the
 // chunk to an FP64 accumulator: FP64 work is 1/4 per element (B300's FP64 rate
 // is low) while the rounding stays at FP32 level per chunk of 4.
@@ -372,26 +327,38 @@ __device__ __forceinline__ float red_chunk(int mode, float a, float b, float c, 
 __global__ void __launch_bounds__(256) k_reduce(int64_t n, const float* __restrict__ a,
                                                 const float* __restrict__ b, int mode,
                                                 double* __restrict__ partial) {
-  double acc = red_init(mode);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool vec = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
   const int64_t n4 = vec ? n / 4 : 0;
+  const bool extremum = mode == 2 || mode == 4 || mode == 5;
+  // max / min are exact in FP32; NaNs are tracked separately (fmaxf drops them)
+  float ext = mode == 5 ? CUDART_INF_F : (mode == 4 ? -CUDART_INF_F : 0.0f);
+  bool nan = false;
+  KahanF sum;
   for (int64_t i = t0; i < n4; i += stride) {
     const float4 x = __ldg(reinterpret_cast<const float4*>(a) + i);
     const float4 y = b ? __ldg(reinterpret_cast<const float4*>(b) + i) : x;
-    float c = red_chunk(mode, red_term(mode, x.x, y.x), red_term(mode, x.y, y.y),
-                        red_term(mode, x.z, y.z), red_term(mode, x.w, y.w));
-    // keep a NaN visible to the max / min modes (fmaxf drops it)
-    if ((mode == 2 || mode == 4 || mode == 5) &&
-        (x.x != x.x || x.y != x.y || x.z != x.z || x.w != x.w))
-      c = __int_as_float(0x7fffffff);
-    acc = red_combine(mode, acc, (double)c);
+    const float c = red_chunk(mode, red_term(mode, x.x, y.x), red_term(mode, x.y, y.y),
+                              red_term(mode, x.z, y.z), red_term(mode, x.w, y.w));
+    if (extremum) {
+      nan |= (x.x != x.x) | (x.y != x.y) | (x.z != x.z) | (x.w != x.w);
+      ext = mode == 5 ? fminf(ext, c) : fmaxf(ext, c);
+    } else {
+      sum.add(c);
+    }
   }
   for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
     const float x = a[i], y = b ? b[i] : x;
-    acc = red_combine(mode, acc, (double)red_term(mode, x, y));
+    const float c = red_term(mode, x, y);
+    if (extremum) {
+      nan |= (x != x);
+      ext = mode == 5 ? fminf(ext, c) : fmaxf(ext, c);
+    } else {
+      sum.add(c);
+    }
   }
+  double acc = extremum ? (nan ? CUDART_NAN : (double)ext) : sum.value();
   const double v = block_red(mode, acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = v;
 }
@@ -414,7 +381,7 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n4, const double* __
   const bool ok = q > 0.0 && isfinite(q) && isfinite(p);
   const float kappa = ok ? (float)(p / q) : 0.0f;
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) *flag = 1;
-  double acc = 0.0;
+  KahanF acc;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
     float4 rv = r[i];
@@ -428,9 +395,9 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n4, const double* __
       rv.z = fmaf(-kappa, hv.z, rv.z); rv.w = fmaf(-kappa, hv.w, rv.w);
       r[i] = rv;
     }
-    acc += (double)((rv.x * rv.x + rv.y * rv.y) + (rv.z * rv.z + rv.w * rv.w));
+    acc.add((rv.x * rv.x + rv.y * rv.y) + (rv.z * rv.z + rv.w * rv.w));
   }
-  const double b = block_sum(acc);
+  const double b = block_sum(acc.value());
   if (threadIdx.x == 0) partial[blockIdx.x] = b;
 }
 
@@ -636,48 +603,55 @@ ProfileRange::~ProfileRange() {
 
 // ---------------------------------------------------------------- launchers
 
-static int g_num_sms = 0;
+static std::atomic<int> g_num_sms{0};
 static int vec_blocks(int64_t n) {
-  if (g_num_sms == 0) {
-    int dev = 0;
+  if (g_num_sms.load() == 0) {
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms.store(sms > 0 ? sms : 148);
   }
   int64_t want = (n + 255) / 256;
   int64_t cap = (int64_t)g_num_sms * 16;
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-static const size_t kTraceSmem = BRICK_FLOATS * sizeof(float);
-static const size_t kBrickSmem = BRICK_FLOATS * sizeof(float);
+thread_local const Tuning* tl_tune = nullptr;
+int tuned_sl_t1() { return tl_tune ? tl_tune->sl_t1 : TB1; }
+int tuned_march_t1() { return tl_tune ? tl_tune->march_t1 : MT1; }
+
 static void brick_attributes() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTraceSmem);
-  cudaFuncSetAttribute(k_sl<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBrickSmem);
-  cudaFuncSetAttribute(k_sl<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBrickSmem);
-  done = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int mx = brick_floats(16) * (int)sizeof(float);
+    cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_sl<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_sl<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  });
 }
 void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht,
                   cudaStream_t st) {
   brick_attributes();
+  const int t1 = tuned_sl_t1();
   ProfileRange pr(K_TRACE, (double)g.N * (12 + 12 * ((df != nullptr) + (db != nullptr))), st);
-  k_trace<<<brick_grid(g), dim3(32, TB2), kTraceSmem, st>>>(g, v, df, db, ht);
+  k_trace<<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
+      g, v, df, db, ht, t1);
 }
 void launch_sl(const Grid& g, const float* u, const float* d, const float* scale, float sigma,
                const float* aux, float beta, float* out, cudaStream_t st) {
   ProfileRange pr(K_SL, (double)g.N * (20 + 4 * (scale != nullptr) + 4 * (aux != nullptr)), st);
   brick_attributes();
-  k_sl<0><<<brick_grid(g), dim3(32, TB2), kBrickSmem, st>>>(g, u, d, scale, sigma, aux, beta,
-                                                             0.f, out);
+  const int t1 = tuned_sl_t1();
+  k_sl<0><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
+      g, u, d, scale, sigma, aux, beta, 0.f, out, t1);
 }
 void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float ht, float* c,
                            cudaStream_t st) {
   ProfileRange pr(K_ADJFAC, (double)g.N * 20, st);
   brick_attributes();
-  k_sl<1><<<brick_grid(g), dim3(32, TB2), kBrickSmem, st>>>(g, D, db, nullptr, 1.f, nullptr,
-                                                             0.f, ht, c);
+  const int t1 = tuned_sl_t1();
+  k_sl<1><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
+      g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1);
 }
 void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st) {
   ProfileRange pr(K_GRAD8, (double)g.N * 16, st);
@@ -694,10 +668,11 @@ static bool launch_march(const Grid& g, const float* mhist, const float* lhist, 
                          float scale0, const float* base, float base_coef, float* out, int nt,
                          cudaStream_t st, const float* dotv = nullptr,
                          double* partial = nullptr) {
-  const dim3 grid = march_grid(g), block(32, MT2);
+  const int mt1 = tuned_march_t1();
+  const dim3 grid = march_grid(g, mt1), block(32, MT2);
 #define CLAIRE_MARCH(NF)                                                                  \
   k_hist_march<MODE, NF><<<grid, block, 0, st>>>(g, mhist, lhist, vt, scale0, base,       \
-                                                 base_coef, out, dotv, partial)
+                                                 base_coef, out, dotv, partial, mt1)
   switch (nt) {
     case 1: CLAIRE_MARCH(2); return true;
     case 2: CLAIRE_MARCH(3); return true;
@@ -709,7 +684,7 @@ static bool launch_march(const Grid& g, const float* mhist, const float* lhist, 
 }
 
 int march_blocks(const Grid& g) {
-  const dim3 m = march_grid(g);
+  const dim3 m = march_grid(g, tuned_march_t1());
   return (int)(m.x * m.y * m.z);
 }
 bool march_supported(int nt) { return nt == 1 || nt == 2 || nt == 4 || nt == 8; }

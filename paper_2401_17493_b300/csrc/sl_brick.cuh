@@ -16,7 +16,9 @@
 
 namespace claire {
 
-constexpr int TB1 = 8, TB2 = 8, TB3 = 32;      // tile: x1 (loop), x2 (threadIdx.y), x3 (lane)
+// tile: x1 (loop, depth t1 chosen at launch from {4, 8, 16} by the autotuner),
+// x2 (threadIdx.y), x3 (lane)
+constexpr int TB1 = 8, TB2 = 8, TB3 = 32;      // TB1: default depth
 constexpr int HB_LO = 3, HB_HI = 3;            // x1 / x2 halo: floor(d) in [-2, 1]
 constexpr int HB3_LO = 4, HB3_HI = 4;          // x3 halo (float4 aligned): floor(d) in [-3, 2]
 constexpr int BB1 = TB1 + HB_LO + HB_HI;       // 14
@@ -26,22 +28,27 @@ constexpr int BX3 = TB3 + HB3_LO + HB3_HI;     // 40 staged floats per row
 // lanes whose displacement floors put them in different rows or planes read
 // disjoint banks (only an x3 span wider than 32 words can still conflict).
 constexpr int BB3 = 64;
-constexpr int BRICK_FLOATS = BB1 * BB2 * BB3;  // 12544 floats = 49 KiB
+constexpr int BRICK_FLOATS = BB1 * BB2 * BB3;  // 12544 floats = 49 KiB at depth 8
+__host__ __device__ inline int brick_rows(int t1) { return (t1 + HB_LO + HB_HI) * BB2; }
+__host__ __device__ inline int brick_floats(int t1) { return brick_rows(t1) * BB3; }
 constexpr int BRICK_THREADS = 32 * TB2;        // 256
 
-__host__ inline dim3 brick_grid(const Grid& g) {
-  return dim3((g.n3 + TB3 - 1) / TB3, (g.n2 + TB2 - 1) / TB2, (g.n1 + TB1 - 1) / TB1);
+__host__ inline dim3 brick_grid(const Grid& g, int t1 = TB1) {
+  return dim3((g.n3 + TB3 - 1) / TB3, (g.n2 + TB2 - 1) / TB2, (g.n1 + t1 - 1) / t1);
 }
 
-// Stage field u over the tile of (i1_0, i2_0, i3_0) plus halo into s[BB1][BB2][BB3].
+// Stage field u over the tile of (i1_0, i2_0, i3_0) plus halo into
+// s[t1 + 6][BB2][BB3] (t1 = tile depth along x1).
 __device__ __forceinline__ void stage_brick(const float* __restrict__ u, const Grid& g, int i1_0,
-                                            int i2_0, int i3_0, float* __restrict__ s) {
+                                            int i2_0, int i3_0, float* __restrict__ s,
+                                            int t1 = TB1) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const int x3s = i3_0 - HB3_LO;
   const bool vec = (g.n3 % 4 == 0) && x3s >= 0 && x3s + BX3 <= g.n3 &&
                    ((reinterpret_cast<uintptr_t>(u) & 15) == 0);
   constexpr int Q = BX3 / 4;                         // float4 per staged row
-  for (int item = tid; item < BB1 * BB2 * Q; item += BRICK_THREADS) {
+  const int nitems = brick_rows(t1) * Q;
+  for (int item = tid; item < nitems; item += BRICK_THREADS) {
     const int row = item / Q, q = item - row * Q;
     const int r1 = row / BB2, r2 = row - r1 * BB2;
     const int g1 = wrap_any(i1_0 - HB_LO + r1, g.n1);

@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--only", default=None)
+    ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 FP16 field storage")
     args = ap.parse_args()
     import torch
     from paper_2401_17493_b300 import build, claire, synth
@@ -36,7 +37,7 @@ def main():
     gen = torch.Generator(device="cuda").manual_seed(0)
     u = torch.rand(shape, device="cuda", generator=gen)
     v = torch.from_numpy(synth.bandlimited_velocity(shape, 8, 4.0, 3).astype(np.float32)).cuda()
-    ctx = claire.Context(shape, nt=4)
+    ctx = claire.Context(shape, nt=4, precision=args.precision)
     ctx.set_images(u, u)
     d, _ = ctx.trace(v)
     out1 = torch.empty(shape, device="cuda")
@@ -80,7 +81,7 @@ def main():
         ms = p["ms"] / p["timed"]
         res[name] = {"ms": ms, "GB/s": p["bytes"] / p["launches"] / (ms * 1e-3) / 1e9,
                      "bytes_per_launch": p["bytes"] / p["launches"]}
-    print(json.dumps({"size": n, "kernels": res}))
+    print(json.dumps({"size": n, "precision": args.precision, "kernels": res}))
     ctx.close()
 
 

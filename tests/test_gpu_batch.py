@@ -1,0 +1,95 @@
+"""Batched solves over uneven grids, CUDA-graph PCG iterations and the
+autotuner: each must give the same registrations as the plain sequential
+per-pair solve (the kernels are deterministic; graph replay runs the same
+launches; tile shapes change only the block partition of the FP64 sums)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2401_17493_b300 import synth
+
+SHAPES = [(32, 32, 32), (48, 40, 34), (64, 64, 64), (40, 48, 56)]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def claire():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_17493_b300 import build
+    build.build()
+    from paper_2401_17493_b300 import claire as C
+    C.load_library()
+    return C
+
+
+def _contexts(C, **opts):
+    ctxs = []
+    for i, shape in enumerate(SHAPES):
+        m0, m1, _ = synth.blob_pair(shape, seed=100 + i, kmax=3, max_disp_voxels=2.0)
+        ctx = C.Context(shape, nt=4, beta_v=5e-3, **opts)
+        ctx.set_images(dev(m0), dev(m1))
+        ctxs.append(ctx)
+    return ctxs
+
+
+def test_batched_solve_equals_sequential_solves(claire):
+    seq = []
+    for ctx in _contexts(claire):
+        v, st = ctx.solve()
+        seq.append((v.cpu().numpy(), st.matvecs, st.status))
+        ctx.close()
+    ctxs = _contexts(claire)
+    vs, stats = claire.solve_batch(ctxs)
+    for (vref, mv, status), v, st in zip(seq, vs, stats):
+        assert st.status == status and st.matvecs == mv
+        assert np.array_equal(v.cpu().numpy(), vref)
+    for c in ctxs:
+        c.close()
+
+
+def test_batched_continuation(claire):
+    betas = [5e-2, 5e-3]
+    ctxs = _contexts(claire)
+    vs, stats = claire.solve_batch(ctxs, betas=betas, max_threads=2)
+    for ctx, v, st in zip(ctxs, vs, stats):
+        assert st.grad_rel <= 5e-2 and st.J < st.J0
+        v2, st2 = ctx.solve_continuation(betas)
+        assert np.array_equal(v.cpu().numpy(), v2.cpu().numpy())
+        ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replayed_pcg_equals_launch_by_launch(claire, precision):
+    shape = SHAPES[1]
+    m0, m1, _ = synth.blob_pair(shape, seed=7, kmax=3, max_disp_voxels=2.0)
+    out = []
+    for graphs in (0, 1):
+        with claire.Context(shape, nt=4, beta_v=1e-2, graphs=graphs, precision=precision) as ctx:
+            ctx.set_images(dev(m0), dev(m1))
+            v, st = ctx.solve_continuation([1e-1, 1e-2])
+            torch.cuda.synchronize()
+            out.append((v.cpu().numpy(), st.matvecs, st.pcg_iters))
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_autotuner_picks_valid_shapes_and_keeps_results(claire):
+    shape = SHAPES[2]
+    m0, m1, _ = synth.blob_pair(shape, seed=8, kmax=3, max_disp_voxels=2.0)
+    with claire.Context(shape, nt=4, beta_v=1e-2, max_newton=2, max_pcg=8,
+                        fixed_iters=1) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        v0, _ = ctx.solve()
+        sl_t1, march_t1 = ctx.autotune()
+        assert sl_t1 in (4, 8, 16) and march_t1 in (8, 16, 32, 64)
+        v1, _ = ctx.solve()
+    a, b = v1.cpu().numpy(), v0.cpu().numpy()
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
