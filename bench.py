@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--matvecs", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-pair batched workload")
+    ap.add_argument("--batch-pairs", type=int, default=32)
     return ap.parse_args()
 
 
@@ -127,6 +129,75 @@ def workload(n):
     return m0, m1
 
 
+BATCH_GRIDS = [(64, 64, 64), (96, 112, 80), (128, 128, 128), (160, 192, 144), (192, 192, 192)]
+BATCH_BETA = 5e-3
+
+
+def _batch_pair(seed):
+    import numpy as np
+    from paper_2401_17493_b300 import synth
+    rng = np.random.default_rng(seed)
+    shape = BATCH_GRIDS[int(rng.integers(0, len(BATCH_GRIDS)))]
+    m0, m1, _ = synth.ellipsoid_pair(shape, seed=seed)
+    return shape, m0, m1
+
+
+def batch_workload(npairs):
+    """Seeded pairs 1000.. on grids drawn uniformly from BATCH_GRIDS (generated in
+    spawned worker processes: no fork after CUDA initialisation)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_pair, range(1000, 1000 + npairs)))
+
+
+def run_batch(args, pairs):
+    """Uneven-grid batch: sequential per-pair solves vs claire_solve_batch
+    (concurrent streams, CUDA-graph PCG iterations), beta_v 5e-3, nt 4."""
+    import numpy as np
+    import torch
+    from paper_2401_17493_b300 import claire
+    ctxs, vs = [], []
+    for shape, m0, m1 in pairs:
+        ctx = claire.Context(shape, nt=NT, beta_v=BATCH_BETA, eps_opt=EPS_OPT, max_pcg=MAX_PCG,
+                             graphs=1)
+        ctx.set_images(torch.from_numpy(m0).cuda(), torch.from_numpy(m1).cuda())
+        ctxs.append(ctx)
+        vs.append(torch.zeros((3,) + shape, device="cuda"))
+    for ctx, v in zip(ctxs, vs):                       # warm-up: plans, graphs, caches
+        v.zero_()
+        ctx.solve(v)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_stats = []
+    for ctx, v in zip(ctxs, vs):
+        v.zero_()
+        seq_stats.append(ctx.solve(v)[1])
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    v_seq = [v.clone() for v in vs]
+    for v in vs:
+        v.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, bstats = claire.solve_batch(ctxs, vs)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    same = all(torch.equal(a, b) for a, b in zip(v_seq, vs))
+    voxels = sum(int(np.prod(c.shape)) for c in ctxs)
+    for c in ctxs:
+        c.close()
+    return {"pairs": len(ctxs), "grids": sorted(set(str(c) for c, _, _ in pairs)),
+            "voxels": voxels, "sequential_s": t_seq, "batched_s": t_batch,
+            "speedup": t_seq / t_batch, "pairs_per_s": len(ctxs) / t_batch,
+            "matvecs": int(sum(st.matvecs for st in bstats)),
+            "all_converged": all(st.grad_rel <= EPS_OPT for st in bstats),
+            "batched_equals_sequential": bool(same),
+            "workload": "ellipsoid phantom pairs seeds 1000.., grids from {64^3, 96x112x80, "
+                        "128^3, 160x192x144, 192^3}, beta_v 5e-3, nt 4, rel-grad 5e-2"}
+
+
 def cpu_oracle_sample(m0, m1, n_full):
     """FP64 oracle continuation solve of the workload restricted to 32^3, scaled by
     the voxel ratio to the full grid (the 256^3 solve takes more iterations, so the
@@ -188,6 +259,9 @@ def run_claire(args, world, rank, local):
     n = args.size
     shape = (n, n, n)
     m0, m1 = workload(n)
+    pairs = None
+    if not args.no_batch and rank == 0 and world == 1:
+        pairs = batch_workload(args.batch_pairs)     # before any CUDA call of this process
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     m0d, m1d = dev(m0), dev(m1)
     ctx = claire.Context(shape, nt=NT, beta_v=BETAS[0], eps_opt=EPS_OPT, max_newton=50,
@@ -300,6 +374,8 @@ def run_claire(args, world, rank, local):
     interp_gbs = interp_bytes / (interp_ms * 1e-3) / 1e9
     total_kernel_ms = sum(p["ms"] for p in prof.values())
 
+    batch = run_batch(args, pairs) if pairs is not None else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, raw, _ = cpu_oracle_sample(m0, m1, n)
@@ -319,6 +395,7 @@ def run_claire(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single"},
         "matvecs_per_s": matvecs_per_s,
         "mixed": mixed,
+        "batch": batch,
         "interp_fd_hbm_frac": interp_gbs / peak,
         "interp_fd_gbs": interp_gbs,
         "solve": {"newton_iters": st0["newton_iters"], "pcg_iters": st0["pcg_iters"],
