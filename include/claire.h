@@ -221,6 +221,67 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
  * nothing has been evaluated yet.  The chosen shapes are returned (NULL ok). */
 claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
 
+/* ---- learned warm start: 3D U-Net kernels --------------------------------------
+ * Not part of the paper: a small 3D U-Net predicts an initial velocity from
+ * the image pair on a 64^3 grid.  Activations are channels-last BF16 [V][C]
+ * (V = batch B x D x H x W voxels, W fastest); weights BF16 [Cout][27][Cin];
+ * accumulation FP32.  All convolutions are 3x3x3 with periodic padding and run
+ * as implicit GEMMs on the tensor cores.  All pointers are device pointers
+ * owned by the caller; calls are asynchronous on the given stream (NULL =
+ * legacy default stream) and only report launch errors.
+ *
+ * Forward: y = act(conv(x, w) + bias); act = ReLU when relu != 0.  cin and cout
+ * multiples of 16; y_bf16 ([V][cout] BF16) and / or y_f32 ([V][cout]) may be
+ * NULL (not both); bias ([cout]) may be NULL. */
+claire_status claire_conv3d_forward(const void* x, int B, int D, int H, int W, int cin,
+                                    const void* w, const float* bias, int cout, int relu,
+                                    void* y_bf16, float* y_f32, void* stream);
+/* wf[cin][27][cout] = w[cout][26 - t][cin]: the data gradient of a conv is
+ * claire_conv3d_forward of dy with wf (cin and cout swapped, no bias / ReLU). */
+claire_status claire_conv3d_flip_weights(const void* w, int cout, int cin, void* wf,
+                                         void* stream);
+/* Weight gradient dw[cout][27][cin] (FP32) = sum_v dy[v][n] x[nbr_t(v)][c], as
+ * nsplit voxel chunks written to partial (nsplit x cout x 27 x cin floats) and
+ * summed in a fixed order.  cin in {16, 32, 48, 64, 96, 128, 192}. */
+claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int cin,
+                                  const void* dy, int cout, float* partial, int nsplit,
+                                  float* dw, void* stream);
+/* Layer helpers (BF16 channels-last), op:
+ *  0 ReLU backward: b (dy) *= (a (y) > 0), V x C elements
+ *  1 / 2  2x2x2 average pool forward a -> b / backward a (dy coarse) -> b (dx fine);
+ *         (B, D, H, W) = fine grid, C channels
+ *  3 / 4  nearest 2x upsampling of a [coarse][C] into channels [c_off, c_off + C)
+ *         of b [fine][Cdst] / its adjoint (sum of the 8 children) from a into b;
+ *         (B, D, H, W) = coarse grid
+ *  5 / 6  copy a [V][C] into channels [c_off, c_off + C) of b [V][Cdst] / back out
+ *  7      b += a (V x C elements) */
+claire_status claire_unet_op(int op, const void* a, void* b, long long V, int C, int Cdst,
+                             int c_off, int B, int D, int H, int W, void* stream);
+/* db[c] = sum_v dy[v][c] (FP32, fixed order). */
+claire_status claire_unet_bias_grad(const void* dy, long long V, int C, float* db,
+                                    void* stream);
+/* out[v][c] = BF16(scale * f[c][v]) for c < nf, 0 for nf <= c < C. */
+claire_status claire_unet_pack(long long V, int nf, const float* f, float scale, int C,
+                               void* out, void* stream);
+/* On the first 3 channels of y ([V][C] FP32): pred[c][v] = scale y[v][c] (pred
+ * may be NULL); with target ([3][V]) also loss = mean squared error (needs
+ * partial with nblocks doubles, written to *loss on the device) and its
+ * gradient dy ([V][C] BF16, zero in channels >= 3; may be NULL). */
+claire_status claire_unet_mse(long long V, int C, const float* y, const float* target,
+                              float scale, void* dy, float* pred, double* partial, int nblocks,
+                              double* loss, void* stream);
+/* Adam step on FP32 master weights p with gradient g and moments m, v (step
+ * >= 1 for the bias corrections); pb (BF16 copy of p) may be NULL. */
+claire_status claire_unet_adam(long long n, float* p, const float* g, float* m, float* v,
+                               float lr, float b1, float b2, float eps, int step, void* pb,
+                               void* stream);
+/* Spectral resampling of ncomp planar fields [ncomp][n1][n2][n3] onto an
+ * m1 x m2 x m3 grid (Sec. 2.5.6, spectral restriction / prolongation): keeps
+ * the Fourier modes with |k_i| < min(n_i, m_i) / 2, zero elsewhere.  Even
+ * sizes.  Allocates temporary cuFFT plans and buffers; synchronous. */
+claire_status claire_resample(int n1, int n2, int n3, const float* in, int m1, int m2, int m3,
+                              float* out, int ncomp, void* stream);
+
 /* ---- launch accounting ---------------------------------------------------
  * The context counts every kernel it launches by class, with the algorithmic
  * bytes each launch moves (each input field read once, each output written

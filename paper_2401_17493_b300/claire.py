@@ -25,6 +25,9 @@ EXPORTED = [
     "claire_trace", "claire_interp", "claire_grad8", "claire_div8", "claire_spectral",
     "claire_det_deformation_gradient", "claire_profile_reset", "claire_profile_read",
     "claire_transport_noalloc", "claire_autotune", "claire_solve_batch",
+    "claire_conv3d_forward", "claire_conv3d_flip_weights", "claire_conv3d_wgrad",
+    "claire_unet_op", "claire_unet_bias_grad", "claire_unet_pack", "claire_unet_mse",
+    "claire_unet_adam", "claire_resample",
 ]
 
 
@@ -106,6 +109,16 @@ def load_library(path=LIB_PATH):
         "claire_autotune": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "claire_solve_batch": ([ctypes.POINTER(P), I, ctypes.POINTER(D), I,
                                 ctypes.POINTER(P), ctypes.POINTER(Stats), I], I),
+        "claire_conv3d_forward": ([P, I, I, I, I, I, P, P, I, I, P, P, P], I),
+        "claire_conv3d_flip_weights": ([P, I, I, P, P], I),
+        "claire_conv3d_wgrad": ([P, I, I, I, I, I, P, I, P, I, P, P], I),
+        "claire_unet_op": ([I, P, P, ctypes.c_longlong, I, I, I, I, I, I, I, P], I),
+        "claire_unet_bias_grad": ([P, ctypes.c_longlong, I, P, P], I),
+        "claire_unet_pack": ([ctypes.c_longlong, I, P, ctypes.c_float, I, P, P], I),
+        "claire_unet_mse": ([ctypes.c_longlong, I, P, P, ctypes.c_float, P, P, P, I, P, P], I),
+        "claire_unet_adam": ([ctypes.c_longlong, P, P, P, P, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, I, P, P], I),
+        "claire_resample": ([I, I, I, P, I, I, I, P, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

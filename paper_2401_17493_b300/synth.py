@@ -12,6 +12,8 @@ RNG: numpy PCG64 (``np.random.default_rng(seed)``).  All coordinates are in
 voxel units on the periodic grid [0, n_i).
 """
 
+import math
+
 import numpy as np
 
 
@@ -178,3 +180,60 @@ def smooth_field(shape, kmax, seed, amplitude=1.0):
     """A band-limited scalar field (for operator-level tests)."""
     f = bandlimited_field(shape, kmax, _rng(seed), 1)[0]
     return (amplitude * f / np.max(np.abs(f))).astype(np.float64)
+
+
+# ------------------------------------------------ GPU generator (torch)
+
+def ellipsoid_pair_torch(shape, seed, kmax=8, max_disp_voxels=4.0, noise=0.02,
+                         smooth_voxels=1.0, device="cuda"):
+    """The ellipsoid phantom pair of ellipsoid_pair, evaluated on the GPU.
+
+    Same formulas; the ellipsoid parameters come from numpy's PCG64 with
+    `seed`, the noise and the band-limited displacement from a torch
+    generator seeded with `seed` (so the arrays differ from ellipsoid_pair's
+    for the same seed, but the family is the same).  For large seeded data
+    sets (training pairs of the learned warm start).  Returns float32 CUDA
+    tensors (m0, m1).
+    """
+    import torch
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    n = torch.tensor(shape, dtype=torch.float64)
+    centre, axes, levels = ellipsoid_params(shape, seed)
+    n1, n2, n3 = shape
+    # band-limited displacement (voxel units), max norm max_disp_voxels
+    k1 = torch.fft.fftfreq(n1, 1.0 / n1, device=device)[:, None, None]
+    k2 = torch.fft.fftfreq(n2, 1.0 / n2, device=device)[None, :, None]
+    k3 = torch.arange(n3 // 2 + 1, device=device, dtype=torch.float32)[None, None, :]
+    mask = (k1 ** 2 + k2 ** 2 + k3 ** 2) <= kmax ** 2
+    u = []
+    for _ in range(3):
+        re = torch.randn(mask.shape, generator=gen, device=device)
+        im = torch.randn(mask.shape, generator=gen, device=device)
+        u.append(torch.fft.irfftn(torch.complex(re, im) * mask, s=shape, dim=(0, 1, 2)))
+    u = torch.stack(u)
+    u *= max_disp_voxels / torch.sqrt((u ** 2).sum(0)).max()
+    grid = torch.meshgrid(*[torch.arange(m, device=device, dtype=torch.float32) for m in shape],
+                          indexing="ij")
+    kf = [torch.fft.fftfreq(n1, device=device)[:, None, None],
+          torch.fft.fftfreq(n2, device=device)[None, :, None],
+          torch.fft.rfftfreq(n3, device=device)[None, None, :]]
+    gauss = torch.exp(-2.0 * (math.pi * smooth_voxels) ** 2 * (kf[0] ** 2 + kf[1] ** 2 + kf[2] ** 2))
+    out = []
+    for warp in (False, True):
+        x = [grid[i] - u[i] if warp else grid[i] for i in range(3)]
+        d = []
+        for i in range(3):
+            di = x[i] - float(centre[i])
+            d.append(di - shape[i] * torch.round(di / shape[i]))
+        img = torch.zeros(shape, device=device)
+        prev = 0.0
+        for ax, lev in zip(axes, levels):
+            rho = torch.sqrt(sum((d[i] / float(ax[i])) ** 2 for i in range(3)))
+            dist = (rho - 1.0) * float(np.mean(ax))
+            img += (lev - prev) * 0.5 * (1.0 - torch.tanh(dist / 2.0))
+            prev = lev
+        img += noise * torch.randn(shape, generator=gen, device=device)
+        img = torch.fft.irfftn(torch.fft.rfftn(img) * gauss, s=shape, dim=(0, 1, 2))
+        out.append(img.float().contiguous())
+    del n
+    return out[0], out[1]
