@@ -278,7 +278,11 @@ claire_status claire_unet_adam(long long n, float* p, const float* g, float* m, 
 /* Spectral resampling of ncomp planar fields [ncomp][n1][n2][n3] onto an
  * m1 x m2 x m3 grid (Sec. 2.5.6, spectral restriction / prolongation): keeps
  * the Fourier modes with |k_i| < min(n_i, m_i) / 2, zero elsewhere.  Even
- * sizes.  Allocates temporary cuFFT plans and buffers; synchronous. */
+ * sizes; ncomp * n1 * n2 * (n3/2+1) < 2^31.  Asynchronous on stream.  The
+ * first call for a (device, stream, shapes, ncomp) creates batched cuFFT plans
+ * and two spectral buffers that are kept for the process lifetime (the warm
+ * start resamples once per registration, and plan creation costs milliseconds);
+ * later calls allocate nothing.  The stream must stay valid while it is used. */
 claire_status claire_resample(int n1, int n2, int n3, const float* in, int m1, int m2, int m3,
                               float* out, int ncomp, void* stream);
 

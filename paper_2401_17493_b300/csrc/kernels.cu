@@ -670,9 +670,10 @@ static bool launch_march(const Grid& g, const float* mhist, const float* lhist, 
                          double* partial = nullptr) {
   const int mt1 = tuned_march_t1();
   const dim3 grid = march_grid(g, mt1), block(32, MT2);
-#define CLAIRE_MARCH(NF)                                                                  \
-  k_hist_march<MODE, NF><<<grid, block, 0, st>>>(g, mhist, lhist, vt, scale0, base,       \
-                                                 base_coef, out, dotv, partial, mt1)
+#define CLAIRE_MARCH(NF)                                                                    \
+  k_hist_march<MODE, NF, float><<<grid, block, 0, st>>>(g, mhist, lhist, vt, scale0, nullptr, \
+                                                        base, base_coef, 1.f, out, out, dotv,  \
+                                                        partial, mt1)
   switch (nt) {
     case 1: CLAIRE_MARCH(2); return true;
     case 2: CLAIRE_MARCH(3); return true;

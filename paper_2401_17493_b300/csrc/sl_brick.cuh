@@ -37,6 +37,16 @@ __host__ inline dim3 brick_grid(const Grid& g, int t1 = TB1) {
   return dim3((g.n3 + TB3 - 1) / TB3, (g.n2 + TB2 - 1) / TB2, (g.n1 + t1 - 1) / t1);
 }
 
+// The staged coordinates lie in [-n, 2n) on every axis when the grid is at
+// least one brick wide (n1 >= t1 + 6, n2 >= BB2, n3 >= BX3): one compare
+// and add instead of an integer modulo per staged chunk.
+__device__ __forceinline__ bool brick_wrap_near(const Grid& g, int t1) {
+  return g.n1 >= t1 + HB_LO + HB_HI && g.n2 >= BB2 && g.n3 >= BX3;
+}
+__device__ __forceinline__ int wrap_sel(int i, int n, bool near) {
+  return near ? wrap_near(i, n) : wrap_any(i, n);
+}
+
 // Stage field u over the tile of (i1_0, i2_0, i3_0) plus halo into
 // s[t1 + 6][BB2][BB3] (t1 = tile depth along x1).
 __device__ __forceinline__ void stage_brick(const float* __restrict__ u, const Grid& g, int i1_0,
@@ -44,19 +54,21 @@ __device__ __forceinline__ void stage_brick(const float* __restrict__ u, const G
                                             int t1 = TB1) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const int x3s = i3_0 - HB3_LO;
-  const bool vec = (g.n3 % 4 == 0) && x3s >= 0 && x3s + BX3 <= g.n3 &&
-                   ((reinterpret_cast<uintptr_t>(u) & 15) == 0);
+  // x3s is a multiple of 4, so with n3 % 4 == 0 a 4-float chunk never
+  // straddles the periodic wrap: edge tiles copy whole wrapped chunks too
+  const bool vec = (g.n3 % 4 == 0) && ((reinterpret_cast<uintptr_t>(u) & 15) == 0);
+  const bool near = brick_wrap_near(g, t1);
   constexpr int Q = BX3 / 4;                         // float4 per staged row
   const int nitems = brick_rows(t1) * Q;
   for (int item = tid; item < nitems; item += BRICK_THREADS) {
     const int row = item / Q, q = item - row * Q;
     const int r1 = row / BB2, r2 = row - r1 * BB2;
-    const int g1 = wrap_any(i1_0 - HB_LO + r1, g.n1);
-    const int g2 = wrap_any(i2_0 - HB_LO + r2, g.n2);
+    const int g1 = wrap_sel(i1_0 - HB_LO + r1, g.n1, near);
+    const int g2 = wrap_sel(i2_0 - HB_LO + r2, g.n2, near);
     const float* src = u + ((int64_t)g1 * g.n2 + g2) * g.n3;
     float* dst = s + row * BB3 + 4 * q;
     if (vec) {
-      cp_async16(dst, src + x3s + 4 * q);
+      cp_async16(dst, src + wrap_sel(x3s + 4 * q, g.n3, near));
     } else {
 #pragma unroll
       for (int e = 0; e < 4; ++e) cp_async4(dst + e, src + wrap_any(x3s + 4 * q + e, g.n3));

@@ -14,6 +14,8 @@
 #include <cufft.h>
 
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
 #include "../../include/claire.h"
 #include "reduce.cuh"
@@ -361,13 +363,17 @@ __global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict
 
 // Half spectrum of an n-grid -> half spectrum of an m-grid: keep the modes with
 // |k_i| < min(n_i, m_i) / 2 on every axis, zero the others (spectral
-// restriction when m < n, zero-padding prolongation when m > n).
+// restriction when m < n, zero-padding prolongation when m > n), scaled by
+// 1/N_n (cuFFT's transforms are unnormalised).  blockIdx.y = component.
 __global__ void k_resample_modes(int n1, int n2, int n3, const cufftComplex* __restrict__ src,
-                                 int m1, int m2, int m3, cufftComplex* __restrict__ dst) {
+                                 int m1, int m2, int m3, cufftComplex* __restrict__ dst,
+                                 float scale) {
   const int mh = m3 / 2 + 1, nh = n3 / 2 + 1;
   const int64_t total = (int64_t)m1 * m2 * mh;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
+  src += (int64_t)blockIdx.y * n1 * n2 * nh;
+  dst += (int64_t)blockIdx.y * total;
   const int j3 = (int)(i % mh);
   const int j2 = (int)((i / mh) % m2);
   const int j1 = (int)(i / ((int64_t)mh * m2));
@@ -379,14 +385,24 @@ __global__ void k_resample_modes(int n1, int n2, int n3, const cufftComplex* __r
   if (abs(k1) < l1 && abs(k2) < l2 && k3 < l3) {
     const int s1 = k1 < 0 ? k1 + n1 : k1, s2 = k2 < 0 ? k2 + n2 : k2;
     val = src[((int64_t)s1 * n2 + s2) * nh + k3];
+    val.x *= scale;
+    val.y *= scale;
   }
   dst[i] = val;
 }
 
-__global__ void k_scale(int64_t n, float a, float* __restrict__ x) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] *= a;
-}
+// Batched cuFFT plans and spectral buffers of one resampling shape, kept for
+// the process lifetime (per device, stream and shape): the warm start restricts
+// and prolongs once per registration, and creating plans costs milliseconds.
+struct ResamplePlan {
+  int dev;
+  cudaStream_t st;
+  int n[3], m[3], ncomp;
+  cufftHandle pf, pi;
+  cufftComplex *a, *b;
+};
+std::mutex g_resample_mu;
+std::vector<ResamplePlan> g_resample_plans;
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -533,32 +549,41 @@ claire_status claire_resample(int n1, int n2, int n3, const float* in, int m1, i
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t Nn = (int64_t)n1 * n2 * n3, Nm = (int64_t)m1 * m2 * m3;
   const int64_t Cn = (int64_t)n1 * n2 * (n3 / 2 + 1), Cm = (int64_t)m1 * m2 * (m3 / 2 + 1);
-  cufftComplex *a = nullptr, *b = nullptr;
-  if (cudaMalloc(&a, Cn * sizeof(cufftComplex)) != cudaSuccess) return CLAIRE_ENOMEM;
-  if (cudaMalloc(&b, Cm * sizeof(cufftComplex)) != cudaSuccess) {
-    cudaFree(a);
-    return CLAIRE_ENOMEM;
-  }
-  cufftHandle pf = 0, pi = 0;
-  claire_status res = CLAIRE_OK;
-  if (cufftPlan3d(&pf, n1, n2, n3, CUFFT_R2C) != CUFFT_SUCCESS ||
-      cufftPlan3d(&pi, m1, m2, m3, CUFFT_C2R) != CUFFT_SUCCESS ||
-      cufftSetStream(pf, st) != CUFFT_SUCCESS || cufftSetStream(pi, st) != CUFFT_SUCCESS) {
-    res = CLAIRE_ECUDA;
-  } else {
-    for (int c = 0; c < ncomp && res == CLAIRE_OK; ++c) {
-      if (cufftExecR2C(pf, (cufftReal*)(in + c * Nn), a) != CUFFT_SUCCESS) res = CLAIRE_ECUDA;
-      k_resample_modes<<<blocks(Cm), 256, 0, st>>>(n1, n2, n3, a, m1, m2, m3, b);
-      if (cufftExecC2R(pi, b, (cufftReal*)(out + c * Nm)) != CUFFT_SUCCESS) res = CLAIRE_ECUDA;
-      k_scale<<<blocks(Nm), 256, 0, st>>>(Nm, 1.0f / (float)Nn, out + c * Nm);
+  if (Nn > INT32_MAX || Nm > INT32_MAX || Cn * ncomp > INT32_MAX) return CLAIRE_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CLAIRE_ECUDA;
+  std::lock_guard<std::mutex> lock(g_resample_mu);
+  ResamplePlan* plan = nullptr;
+  for (auto& p : g_resample_plans)
+    if (p.dev == dev && p.st == st && p.ncomp == ncomp && p.n[0] == n1 && p.n[1] == n2 &&
+        p.n[2] == n3 && p.m[0] == m1 && p.m[1] == m2 && p.m[2] == m3)
+      plan = &p;
+  if (!plan) {
+    ResamplePlan p{dev, st, {n1, n2, n3}, {m1, m2, m3}, ncomp, 0, 0, nullptr, nullptr};
+    int nn[3] = {n1, n2, n3}, mm[3] = {m1, m2, m3};
+    bool ok = cudaMalloc(&p.a, Cn * ncomp * sizeof(cufftComplex)) == cudaSuccess &&
+              cudaMalloc(&p.b, Cm * ncomp * sizeof(cufftComplex)) == cudaSuccess;
+    ok = ok &&
+         cufftPlanMany(&p.pf, 3, nn, nullptr, 1, (int)Nn, nullptr, 1, (int)Cn, CUFFT_R2C,
+                       ncomp) == CUFFT_SUCCESS &&
+         cufftPlanMany(&p.pi, 3, mm, nullptr, 1, (int)Cm, nullptr, 1, (int)Nm, CUFFT_C2R,
+                       ncomp) == CUFFT_SUCCESS &&
+         cufftSetStream(p.pf, st) == CUFFT_SUCCESS && cufftSetStream(p.pi, st) == CUFFT_SUCCESS;
+    if (!ok) {
+      if (p.pf) cufftDestroy(p.pf);
+      if (p.pi) cufftDestroy(p.pi);
+      cudaFree(p.a);
+      cudaFree(p.b);
+      return CLAIRE_ENOMEM;
     }
+    g_resample_plans.push_back(p);
+    plan = &g_resample_plans.back();
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess) res = CLAIRE_ECUDA;
-  if (pf) cufftDestroy(pf);
-  if (pi) cufftDestroy(pi);
-  cudaFree(a);
-  cudaFree(b);
-  return res;
+  if (cufftExecR2C(plan->pf, (cufftReal*)in, plan->a) != CUFFT_SUCCESS) return CLAIRE_ECUDA;
+  k_resample_modes<<<dim3(blocks(Cm), ncomp), 256, 0, st>>>(n1, n2, n3, plan->a, m1, m2, m3,
+                                                           plan->b, 1.0f / (float)Nn);
+  if (cufftExecC2R(plan->pi, plan->b, (cufftReal*)out) != CUFFT_SUCCESS) return CLAIRE_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
 }
 
 }  // extern "C"
