@@ -121,7 +121,12 @@ k_hist_march(Grid g, const T* __restrict__ mhist, const T* __restrict__ lhist,
              const float* __restrict__ base, float base_coef, float umul,
              float* __restrict__ out, T* __restrict__ hout, const float* __restrict__ dotv,
              double* __restrict__ partial, int mt1) {
+  // sp: staged planes as stored (double buffer).  FP16 planes are converted
+  // into the FP32 plane fp by the threads that copied them, once per element,
+  // so the 16 stencil reads per field and node need no conversion.
+  constexpr bool kHalf = sizeof(T) == 2;
   __shared__ __align__(16) T sp[2][NF][MPLANE];
+  __shared__ __align__(16) float fp[kHalf ? NF : 1][kHalf ? MPLANE : 4];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i3_0 = blockIdx.x * MT3, i2_0 = blockIdx.y * MT2, i1_0 = blockIdx.z * mt1;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
@@ -200,21 +205,41 @@ k_hist_march(Grid g, const T* __restrict__ mhist, const T* __restrict__ lhist,
     }
     cp_async_commit();
     cp_async_wait_prev();
+    if constexpr (kHalf) {
+      // convert the chunks (or elements) this thread staged itself
+      if (vec) {
+        if (ch.src >= 0) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const uint2 raw = *reinterpret_cast<const uint2*>(&sp[cur][f][ch.dst]);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+            *reinterpret_cast<float4*>(&fp[f][ch.dst]) = make_float4(a.x, a.y, b.x, b.y);
+          }
+        }
+      } else {
+        const int tid = threadIdx.y * 32 + threadIdx.x;
+        for (int item = tid; item < MPLANE; item += 32 * MT2)
+#pragma unroll
+          for (int f = 0; f < NF; ++f) fp[f][item] = to_f(sp[cur][f][item]);
+      }
+    }
     __syncthreads();                                           // plane i1 staged by all
     if (active) {
       const int64_t idx = (int64_t)i1 * s1 + col;
       float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const T* p = sp[cur][f];
+        const float* p;
+        if constexpr (kHalf) p = fp[f];
+        else p = sp[cur][f];
         const float gx = fd8(q[f][0], q[f][1], q[f][2], q[f][3], q[f][5], q[f][6], q[f][7],
                              q[f][8], g.inv_h1);
-        const float gy = fd8(to_f(p[c - 4 * MP3]), to_f(p[c - 3 * MP3]), to_f(p[c - 2 * MP3]),
-                             to_f(p[c - MP3]), to_f(p[c + MP3]), to_f(p[c + 2 * MP3]),
-                             to_f(p[c + 3 * MP3]), to_f(p[c + 4 * MP3]), g.inv_h2);
-        const float gz = fd8(to_f(p[c - 4]), to_f(p[c - 3]), to_f(p[c - 2]), to_f(p[c - 1]),
-                             to_f(p[c + 1]), to_f(p[c + 2]), to_f(p[c + 3]), to_f(p[c + 4]),
-                             g.inv_h3);
+        const float gy = fd8(p[c - 4 * MP3], p[c - 3 * MP3], p[c - 2 * MP3], p[c - MP3],
+                             p[c + MP3], p[c + 2 * MP3], p[c + 3 * MP3], p[c + 4 * MP3],
+                             g.inv_h2);
+        const float gz = fd8(p[c - 4], p[c - 3], p[c - 2], p[c - 1], p[c + 1], p[c + 2],
+                             p[c + 3], p[c + 4], g.inv_h3);
         if (MODE == 0) {
           float sd = gx * (sig * xc[0]);
           sd = fmaf(gy, sig * xc[1], sd);

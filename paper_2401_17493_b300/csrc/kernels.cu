@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __
                                                          int t1) {
   extern __shared__ __align__(16) float sm[];
   const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
-  const int64_t N = g.N;
+  const int64_t N = g.N, s1 = (int64_t)g.n2 * g.n3;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   const bool active = i2 < g.n2 && i3 < g.n3;
@@ -64,15 +64,25 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __
     for (int c = 0; c < 3; ++c) {
       if (!first) __syncthreads();               // previous brick consumed
       first = false;
+      // v(x) of the next node is loaded one node ahead (the first while the
+      // brick is being staged)
+      const int64_t idx0 = active ? lin(g, i1_0, i2, i3) : 0;
+      float vn[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) vn[a] = active ? v[a * N + idx0] : 0.f;
       stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm, t1);
       __syncthreads();
       if (!active) continue;
       const float ihc = c == 0 ? g.inv_h1 : (c == 1 ? g.inv_h2 : g.inv_h3);
 #pragma unroll 2
       for (int k = 0; k < kmax; ++k) {
-        const int64_t idx = lin(g, i1_0 + k, i2, i3);
-        const float u1 = v[idx] * g.inv_h1, u2 = v[N + idx] * g.inv_h2,
-                    u3 = v[2 * N + idx] * g.inv_h3;    // v(x), grid units per unit time
+        const int64_t idx = idx0 + k * s1;
+        const float u1 = vn[0] * g.inv_h1, u2 = vn[1] * g.inv_h2,
+                    u3 = vn[2] * g.inv_h3;             // v(x), grid units per unit time
+        if (k + 1 < kmax) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) vn[a] = v[a * N + idx + s1];
+        }
         NodeTaps t;
         node_taps(sg * u1, sg * u2, sg * u3, t);
         const float w = taps_in_brick(t) ? gather_brick(sm, t, k, ty, lane)
@@ -100,20 +110,31 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl(Grid g, const float* __res
                                                       int t1) {
   extern __shared__ __align__(16) float sm[];
   const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
-  stage_brick(u, g, i1_0, i2_0, i3_0, sm, t1);
-  __syncthreads();
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
-  if (i2 >= g.n2 || i3 >= g.n3) return;
-  const int64_t N = g.N;
+  const bool active = i2 < g.n2 && i3 < g.n3;
+  const int64_t N = g.N, s1 = (int64_t)g.n2 * g.n3;
+  const int64_t idx0 = active ? lin(g, i1_0, i2, i3) : 0;
+  // departure points of the next node are loaded one node ahead (the first
+  // ones while the brick is being staged)
+  float dn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dn[a] = active ? d[a * N + idx0] : 0.f;
+  stage_brick(u, g, i1_0, i2_0, i3_0, sm, t1);
+  __syncthreads();
+  if (!active) return;
   const int ctr = (HB_LO * BB2 + ty + HB_LO) * BB3 + lane + HB3_LO;
   const int kmax = min(t1, g.n1 - i1_0);
 #pragma unroll 2
   for (int k = 0; k < kmax; ++k) {
     const int i1 = i1_0 + k;
-    const int64_t idx = lin(g, i1, i2, i3);
+    const int64_t idx = idx0 + k * s1;
     NodeTaps t;
-    node_taps(d[idx], d[N + idx], d[2 * N + idx], t);
+    node_taps(dn[0], dn[1], dn[2], t);
+    if (k + 1 < kmax) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dn[a] = d[a * N + idx + s1];
+    }
     const float y = taps_in_brick(t) ? gather_brick(sm, t, k, ty, lane)
                                      : gather_global(u, g, t, i1, i2, i3);
     float r;

@@ -114,19 +114,28 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl_h(Grid g, const __half* __
                                                         int t1) {
   extern __shared__ __align__(16) float smf[];
   const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
-  stage_brick_h32(u, g, i1_0, i2_0, i3_0, smf, t1);
-  __syncthreads();
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
-  if (i2 >= g.n2 || i3 >= g.n3) return;
-  const int64_t N = g.N;
+  const bool active = i2 < g.n2 && i3 < g.n3;
+  const int64_t N = g.N, s1 = (int64_t)g.n2 * g.n3;
+  const int64_t idx0 = active ? lin(g, i1_0, i2, i3) : 0;
+  float dn[3];                                     // departure points, one node ahead
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dn[a] = active ? d[a * N + idx0] : 0.f;
+  stage_brick_h32(u, g, i1_0, i2_0, i3_0, smf, t1);
+  __syncthreads();
+  if (!active) return;
   const int kmax = min(t1, g.n1 - i1_0);
 #pragma unroll 2
   for (int k = 0; k < kmax; ++k) {
     const int i1 = i1_0 + k;
-    const int64_t idx = lin(g, i1, i2, i3);
+    const int64_t idx = idx0 + k * s1;
     NodeTaps t;
-    node_taps(d[idx], d[N + idx], d[2 * N + idx], t);
+    node_taps(dn[0], dn[1], dn[2], t);
+    if (k + 1 < kmax) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dn[a] = d[a * N + idx + s1];
+    }
     const float y = taps_in_brick(t) ? gather_brick(smf, t, k, ty, lane)
                                      : gather_global_h(u, g, t, i1, i2, i3);
     float r = y * (scale ? scale[idx] : sigma);
