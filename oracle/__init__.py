@@ -10,7 +10,7 @@ code, constants, tables or helpers with the CUDA path under
 Everything is NumPy/SciPy in float64.  Each function cites the passage of the
 paper it follows (section, equation label, algorithm).  Where the paper is
 silent or garbled the oracle takes one reading; the readings are named in the
-docstrings by their tag (C-1 ... C-14) and listed together in the design
+docstrings by their tag (C-1 ... C-15) and listed together in the design
 notes of the repository.
 
 Modules
@@ -21,6 +21,7 @@ fd8        8th-order finite-difference gradient/divergence (Sec. 2.5.3)
 spectral   regulariser, preconditioner, Leray, restrict    (Sec. 2.5.3, 2.5.5, Appendix)
 transport  RK2 departure points and the four SL solves     (Sec. 2.5.2, eqs. transport/adjoint/incstate/incadj)
 reduced    objective, reduced gradient, Hessian matvec     (eqs. varopt-claire, rgrad, matvec)
+precond    two-level zero-velocity preconditioner          (Sec. 2.5.6)
 solver     PCG (Algorithm 2), Armijo, Gauss-Newton (Algorithm 1), continuation (Sec. 2.6)
 defgrad    deformation-gradient transport and det F1       (Appendix, eq. def-grad)
 
@@ -31,4 +32,4 @@ near-incompressible weight c(kappa) of ``spectral.near_incompressible_term``
 is only checked through its limits: parity unpinned for that one function.
 """
 
-from . import grid, interp, fd8, spectral, transport, reduced, solver, defgrad  # noqa: F401
+from . import grid, interp, fd8, spectral, transport, reduced, precond, solver, defgrad  # noqa: F401

@@ -1,7 +1,10 @@
 """Inexact Gauss-Newton-Krylov solver (Sec. 2.5.5, 2.5.6, 2.6; Algorithms 1 and 2).
 
 * pcg        Algorithm 2: matrix-free PCG for H v~ = -g with the spectral
-             regularisation preconditioner M = alpha L (Sec. 2.5.6).
+             regularisation preconditioner M = alpha L (Sec. 2.5.6), or the
+             two-level zero-velocity preconditioner of oracle.precond
+             (Options.precond = "two_level"; nested CG tolerance a tenth of
+             the outer PCG's relative tolerance eta).
              Reading C-8: stop when ||r||_2 <= eta ||g||_2 with the superlinear
              forcing eta = min(1/2, sqrt(||g^k||_inf / ||g^0||_inf)) (quadratic:
              without the square root).  Negative curvature <s, H s> <= 0 ends
@@ -22,6 +25,7 @@ import numpy as np
 
 from .reduced import evaluate, evaluate_objective, complete_gradient, hessian_matvec
 from .spectral import apply_reg_inverse
+from .precond import two_level_inverse, coarse_gradient
 
 OK, ENOTCONV, ENEGCURV, ELINESEARCH = 0, 5, 6, 7
 
@@ -34,6 +38,8 @@ class Options:
     fixed_iters: bool = False     # run exactly max_newton x max_pcg (parity runs)
     forcing: str = "superlinear"  # or "quadratic"
     full_newton: bool = False
+    precond: str = "spectral"     # or "two_level" (Sec. 2.5.6)
+    max_inner: int = 100          # nested CG iterations per two-level application
     c1: float = 1e-4
     max_halvings: int = 10
     gabs_tol: float = 1e-6
@@ -46,6 +52,7 @@ class Stats:
     matvecs: int = 0
     pde_solves: int = 0
     linesearch_halvings: int = 0
+    inner_iters: int = 0
     J0: float = 0.0
     J: float = 0.0
     mismatch_rel: float = 0.0
@@ -131,9 +138,19 @@ def gauss_newton(prob, v0=None, opts=None, gnorm0=None, stats=None):
         ratio = gnorm / gnorm0
         eta = min(0.5, np.sqrt(ratio) if opts.forcing == "superlinear" else ratio)
         tol = eta * np.sqrt(dot(ev.g, ev.g))
+        if opts.precond == "two_level":
+            gm_c = coarse_gradient(ev.m[prob.nt])    # H0 at the current m(1)
+
+            def apply_Minv(r):
+                z, inner = two_level_inverse(r, None, prob.beta_v, prob.gamma, 0.1 * eta,
+                                             opts.max_inner, gm_c=gm_c)
+                stats.inner_iters += inner
+                return z
+        else:
+            def apply_Minv(r):
+                return apply_reg_inverse(r, prob.beta_v, prob.gamma)
         vt, its, mv, st = pcg(lambda s: hessian_matvec(prob, ev, s, opts.full_newton),
-                              lambda r: apply_reg_inverse(r, prob.beta_v, prob.gamma),
-                              ev.g, tol, opts.max_pcg, opts.fixed_iters)
+                              apply_Minv, ev.g, tol, opts.max_pcg, opts.fixed_iters)
         stats.pcg_iters += its
         stats.matvecs += mv
         stats.pde_solves += 2 * mv
