@@ -62,6 +62,15 @@ typedef struct {
   int autotune;         /* 1: time the tile-shape variants on the first evaluation of a
                            solve and keep the fastest for this context (default 0)   */
   int graphs;           /* 1: replay each PCG iteration as a captured CUDA graph      */
+  int precond;          /* PCG preconditioner (Sec. 2.5.6).  0: spectral, (beta_v L)^-1
+                           with the zero symbol set to one (default).  1: two-level
+                           zero-velocity H0: R^-1/2 M^-1 R^-1/2 with R = beta_v L, M^-1
+                           the coarse (n/2) solve of I + R^-1/2 (grad m (x) grad m)
+                           R^-1/2 at the current m(1) plus the high-frequency part;
+                           needs every n_i % 4 == 0                                  */
+  int max_inner;        /* nested CG iteration cap of precond 1 (default 50)          */
+  double inner_rtol;    /* > 0: fixed relative tolerance of the nested CG; <= 0: one
+                           tenth of the outer PCG's relative tolerance (Sec. 2.6)    */
 } claire_options;
 
 typedef struct {
@@ -70,6 +79,7 @@ typedef struct {
   double detF_min, detF_max, detF_mean;
   double seconds;       /* device time of the call (CUDA events)                    */
   int status;
+  int inner_iters;      /* nested CG iterations of the two-level preconditioner       */
 } claire_stats;
 
 /* Fill *opt with the defaults listed above.  EINVAL on NULL. */
@@ -151,9 +161,18 @@ claire_status claire_div8(claire_ctx* ctx, const float* w, float* div_w);
 /* Spectral operators on a vector field [3][N] (Sec. 2.5.3, 2.5.6, Appendix):
  * op 0: L = (-Laplacian)^gamma;  1: (beta_v L)^-1 with the zero symbol set to
  * one;  2: P_par (gradient part of the Leray decomposition);  3: c(kappa) P_par
- * (near-incompressible term with options.beta_w). */
-enum { CLAIRE_OP_L = 0, CLAIRE_OP_REG_INV = 1, CLAIRE_OP_LERAY_PAR = 2, CLAIRE_OP_NEAR_INC = 3 };
+ * (near-incompressible term with options.beta_w);  4: (beta_v L)^-1/2 with the
+ * zero symbol set to one (the smoother of the two-level preconditioner). */
+enum { CLAIRE_OP_L = 0, CLAIRE_OP_REG_INV = 1, CLAIRE_OP_LERAY_PAR = 2, CLAIRE_OP_NEAR_INC = 3,
+       CLAIRE_OP_REG_INV_SQRT = 4 };
 claire_status claire_spectral(claire_ctx* ctx, int op, const float* in, float* out);
+
+/* z = M^-1 r (device [3][N]) with the preconditioner of options.precond
+ * (Sec. 2.5.6) at the image m(1) of the last claire_objective_gradient
+ * (EORDER if there is none).  For precond 1 the nested CG runs to
+ * options.inner_rtol (1e-3 when that is <= 0) or options.max_inner
+ * iterations; *inner_iters (may be NULL) receives the count. */
+claire_status claire_precondition(claire_ctx* ctx, const float* r, float* z, int* inner_iters);
 
 /* det F1 of the deformation-gradient transport (Appendix, eq. def-grad) for
  * velocity v: min / max / mean into minmaxmean_host[3]; det_out ([N]) may be NULL. */

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libclaire.so")
-SOURCES = ["kernels.cu", "mixed.cu", "claire_api.cu", "noalloc.cu", "unet.cu"]
+SOURCES = ["kernels.cu", "mixed.cu", "claire_api.cu", "noalloc.cu", "unet.cu", "precond.cu"]
 HEADERS = ["common.cuh", "internal.h", "sl_brick.cuh", "fd8_march.cuh", "reduce.cuh"]
 
 NVCC_FLAGS = [

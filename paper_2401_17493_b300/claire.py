@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libclaire.so")
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENOTCONV, ENEGCURV, ELINESEARCH, ETIMEOUT, EORDER = range(10)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ENOTCONV", "ENEGCURV",
                 "ELINESEARCH", "ETIMEOUT", "EORDER"]
-OP_L, OP_REG_INV, OP_LERAY_PAR, OP_NEAR_INC = 0, 1, 2, 3
+OP_L, OP_REG_INV, OP_LERAY_PAR, OP_NEAR_INC, OP_REG_INV_SQRT = 0, 1, 2, 3, 4
 
 EXPORTED = [
     "claire_default_options", "claire_create", "claire_set_options", "claire_get_options",
@@ -27,7 +27,7 @@ EXPORTED = [
     "claire_transport_noalloc", "claire_autotune", "claire_solve_batch",
     "claire_conv3d_forward", "claire_conv3d_flip_weights", "claire_conv3d_wgrad",
     "claire_unet_op", "claire_unet_bias_grad", "claire_unet_pack", "claire_unet_mse",
-    "claire_unet_adam", "claire_resample",
+    "claire_unet_adam", "claire_resample", "claire_precondition",
 ]
 
 
@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("fixed_iters", ctypes.c_int), ("forcing", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("verbose", ctypes.c_int),
                 ("gnorm0", ctypes.c_double), ("autotune", ctypes.c_int),
-                ("graphs", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("precond", ctypes.c_int),
+                ("max_inner", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -50,7 +51,7 @@ class Stats(ctypes.Structure):
                 ("gnorm0", ctypes.c_double),
                 ("detF_min", ctypes.c_double), ("detF_max", ctypes.c_double),
                 ("detF_mean", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("inner_iters", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +93,7 @@ def load_library(path=LIB_PATH):
         "claire_transport": ([P, P, P], I),
         "claire_objective_gradient": ([P, P, ctypes.POINTER(D), P], I),
         "claire_hessian_matvec": ([P, P, P], I),
+        "claire_precondition": ([P, P, P, ctypes.POINTER(I)], I),
         "claire_solve": ([P, P, ctypes.POINTER(Stats)], I),
         "claire_solve_continuation": ([P, ctypes.POINTER(D), I, P, ctypes.POINTER(Stats)], I),
         "claire_solve_host": ([P, P, P, ctypes.POINTER(D), I, P, ctypes.POINTER(Stats)], I),
@@ -283,6 +285,14 @@ class Context:
         self._check(self.lib.claire_hessian_matvec(self.h, _ptr(vt, self.vshape, "vt"),
                                                    _ptr(out, self.vshape, "Hvt")))
         return out
+
+    def precondition(self, r, out=None):
+        """z = M^-1 r with options.precond at the last evaluation; returns (z, inner iterations)."""
+        out = self._new(self.vshape) if out is None else out
+        its = ctypes.c_int(0)
+        self._check(self.lib.claire_precondition(self.h, _ptr(r, self.vshape, "r"),
+                                                 _ptr(out, self.vshape, "z"), ctypes.byref(its)))
+        return out, its.value
 
     def _solve_status(self, st):
         if st not in (OK, ENOTCONV, ELINESEARCH):

@@ -66,6 +66,15 @@ struct claire_ctx {
   long long graph_launches[8][K_COUNT] = {};
   double graph_bytes[8][K_COUNT] = {};
   float* dbuf0 = nullptr;       // first of the two departure-point buffers
+  // two-level preconditioner (options.precond = 1), allocated on first use
+  Grid gc{};                    // coarse grid, n_i / 2 points per axis
+  cufftHandle tl_r2c1 = 0, tl_c2r1 = 0, tl_r2c3 = 0, tl_c2r3 = 0;
+  cufftComplex *tl_cc = nullptr, *cbuf2 = nullptr;
+  float *tl_gm = nullptr, *tl_mc = nullptr, *tl_b = nullptr, *tl_x = nullptr, *tl_r = nullptr,
+        *tl_p = nullptr, *tl_Ap = nullptr, *tl_q = nullptr;
+  bool tl_ready = false, tl_image = false;
+  double tl_rtol = 1e-3;        // nested CG relative tolerance of the current PCG
+  int tl_iters = 0;             // nested CG iterations not yet counted in the stats
   cudaStream_t own = nullptr;   // private stream for graph capture
   cudaStream_t user = nullptr;  // the stream of the options
   cudaEvent_t e_in = nullptr;   // orders the private stream after the user's stream
@@ -199,7 +208,8 @@ float ht_of(const claire_ctx* c) { return 1.0f / (float)c->nt; }
 bool mixed(const claire_ctx* c) { return c->opt.precision == 1; }
 
 // Slots of the device-side FP64 scalars.
-enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4, SLOT_VMAX = 8 };
+enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4, SLOT_VMAX = 8,
+       SLOT_TL_RR0 = 9, SLOT_TL_RR1 = 10, SLOT_TL_PAP = 11, SLOT_ZERO = 12 /* ..14 */ };
 
 // Power-of-two scale that maps max(|m0|, |m1|) into (1/2, 1] (FP16 state range).
 claire_status image_scale(claire_ctx* c) {
@@ -353,7 +363,7 @@ claire_status matvec(claire_ctx* c, const float* vt, float* Hvt) {
 // ---------------------------------------------------------------- Krylov / Newton
 
 struct Counters {
-  int pcg = 0, matvecs = 0, pde = 0, halvings = 0;
+  int pcg = 0, matvecs = 0, pde = 0, halvings = 0, inner = 0;
 };
 
 // Transport part of the Gauss-Newton matvec (incremental state and adjoint):
@@ -400,9 +410,189 @@ claire_status matvec_transport(claire_ctx* c, const float* vt) {
   return check_launch(c, "matvec transport");
 }
 
+// ---------------------------------------------------------------- two-level preconditioner
+
+claire_status tl_set_streams(claire_ctx* c);
+
+// Coarse grid, cuFFT plans and buffers of the two-level preconditioner.
+claire_status tl_setup(claire_ctx* c) {
+  if (c->tl_ready) return CLAIRE_OK;
+  const Grid& g = c->g;
+  if (g.n1 % 4 || g.n2 % 4 || g.n3 % 4)
+    return fail(c, CLAIRE_EINVAL, "two-level preconditioner needs every n_i %% 4 == 0");
+  Grid& gc = c->gc;
+  gc.n1 = g.n1 / 2; gc.n2 = g.n2 / 2; gc.n3 = g.n3 / 2;
+  gc.N = (int64_t)gc.n1 * gc.n2 * gc.n3;
+  const double tp = 2.0 * M_PI;
+  gc.h1 = (float)(tp / gc.n1); gc.h2 = (float)(tp / gc.n2); gc.h3 = (float)(tp / gc.n3);
+  gc.inv_h1 = (float)(gc.n1 / tp); gc.inv_h2 = (float)(gc.n2 / tp); gc.inv_h3 = (float)(gc.n3 / tp);
+  const int64_t Nc = gc.N;
+  const int64_t Ch = (int64_t)gc.n1 * gc.n2 * (gc.n3 / 2 + 1);
+  const int64_t Nh = (int64_t)g.n1 * g.n2 * (g.n3 / 2 + 1);
+  // (allocations and plans made by an earlier, failed call are kept)
+  float** f3[] = {&c->tl_gm, &c->tl_b, &c->tl_x, &c->tl_r, &c->tl_p, &c->tl_Ap, &c->tl_q};
+  for (auto p : f3)
+    if (!*p) TRY(alloc(c, p, 3 * Nc));
+  if (!c->tl_mc) TRY(alloc(c, &c->tl_mc, Nc));
+  float* p = nullptr;
+  if (!c->tl_cc) {
+    TRY(alloc(c, &p, 3 * Ch * 2));
+    c->tl_cc = (cufftComplex*)p;
+  }
+  if (!c->cbuf2) {
+    TRY(alloc(c, &p, 3 * Nh * 2));
+    c->cbuf2 = (cufftComplex*)p;
+  }
+  int nc[3] = {gc.n1, gc.n2, gc.n3};
+  if ((!c->tl_r2c1 && cufftPlan3d(&c->tl_r2c1, g.n1, g.n2, g.n3, CUFFT_R2C) != CUFFT_SUCCESS) ||
+      (!c->tl_c2r1 && cufftPlan3d(&c->tl_c2r1, gc.n1, gc.n2, gc.n3, CUFFT_C2R) != CUFFT_SUCCESS) ||
+      (!c->tl_r2c3 && cufftPlanMany(&c->tl_r2c3, 3, nc, nullptr, 1, (int)Nc, nullptr, 1, (int)Ch,
+                                    CUFFT_R2C, 3) != CUFFT_SUCCESS) ||
+      (!c->tl_c2r3 && cufftPlanMany(&c->tl_c2r3, 3, nc, nullptr, 1, (int)Ch, nullptr, 1, (int)Nc,
+                                    CUFFT_C2R, 3) != CUFFT_SUCCESS))
+    return fail(c, CLAIRE_ECUDA, "cuFFT plans of the two-level preconditioner");
+  CUDA_TRY(c, cudaMemsetAsync(c->slots + SLOT_ZERO, 0, 3 * sizeof(double), c->st));
+  c->tl_ready = true;
+  return tl_set_streams(c);
+}
+
+claire_status tl_set_streams(claire_ctx* c) {
+  if (!c->tl_ready) return CLAIRE_OK;
+  for (cufftHandle h : {c->tl_r2c1, c->tl_c2r1, c->tl_r2c3, c->tl_c2r3})
+    CUFFT_TRY(c, cufftSetStream(h, c->st));
+  return CLAIRE_OK;
+}
+
+// grad m_c: FD8 gradient of the spectral restriction of m(1) (the last state
+// solve) on the coarse grid, the image of the zero-velocity Hessian H0.
+claire_status tl_update_image(claire_ctx* c) {
+  TRY(tl_setup(c));
+  const Grid& g = c->g;
+  const int64_t N = g.N;
+  const float* m1p = c->mhist + (int64_t)c->nt * N;
+  if (mixed(c)) {
+    launch_tl_unscale_h(N, c->mh + (int64_t)c->nt * N, 1.0f / c->sig_m, c->scr3, c->st);
+    m1p = c->scr3;
+  }
+  const double bytes = 4.0 * N + 8.0 * g.n1 * g.n2 * (g.n3 / 2 + 1);
+  {
+    ProfileRange pr(K_CUFFT, bytes, c->st);
+    CUFFT_TRY(c, cufftExecR2C(c->tl_r2c1, (cufftReal*)m1p, c->cbuf));
+  }
+  const int64_t Ch = (int64_t)c->gc.n1 * c->gc.n2 * (c->gc.n3 / 2 + 1);
+  CUDA_TRY(c, cudaMemsetAsync(c->tl_cc, 0, Ch * sizeof(cufftComplex), c->st));
+  launch_tl_split(g, c->cbuf, c->tl_cc, 1, 0, 0.f, 0.f, (float)(1.0 / (double)N), c->st);
+  {
+    ProfileRange pr(K_CUFFT, bytes / 8, c->st);
+    CUFFT_TRY(c, cufftExecC2R(c->tl_c2r1, c->tl_cc, (cufftReal*)c->tl_mc));
+  }
+  launch_grad8(c->gc, c->tl_mc, c->tl_gm, c->st);
+  TRY(check_launch(c, "two-level image"));
+  c->tl_image = true;
+  return CLAIRE_OK;
+}
+
+// out = (beta_v L)^-1/2 in on the coarse grid (zero symbol set to one).
+claire_status tl_reg_inv_sqrt(claire_ctx* c, const float* in, float* out) {
+  const Grid& gc = c->gc;
+  const double bytes = 3.0 * (4.0 * gc.N + 8.0 * gc.n1 * gc.n2 * (gc.n3 / 2 + 1));
+  {
+    ProfileRange pr(K_CUFFT, bytes, c->st);
+    CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)in, c->tl_cc));
+  }
+  launch_spectral(gc, c->tl_cc, CLAIRE_OP_REG_INV_SQRT, (float)c->beta_v, (float)c->gamma, 0.f,
+                  c->st);
+  {
+    ProfileRange pr(K_CUFFT, bytes, c->st);
+    CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)out));
+  }
+  return CLAIRE_OK;
+}
+
+// z = R^-1/2 M^-1 R^-1/2 r and Lz = beta_v L z (Sec. 2.5.6): the low modes of
+// R^-1/2 r are restricted to the coarse grid, where nested CG solves
+// (I + R^-1/2 (grad m_c (x) grad m_c) R^-1/2) s_c = t_c; s_c is prolonged, the
+// high modes are kept, and R^-1/2 is applied again.  With rz_slot >= 0, <r, z>
+// goes to slots[rz_slot].
+claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz, int rz_slot) {
+  TRY(tl_setup(c));
+  if (!c->tl_image) return fail(c, CLAIRE_EORDER, "two-level preconditioner has no image");
+  const Grid& g = c->g;
+  const Grid& gc = c->gc;
+  const int64_t N = g.N, n3c = 3 * gc.N;
+  const int64_t Ch = (int64_t)gc.n1 * gc.n2 * (gc.n3 / 2 + 1);
+  const double fft_f = 3.0 * (4.0 * N + 8.0 * g.n1 * g.n2 * (g.n3 / 2 + 1));
+  const double fft_c = 3.0 * (4.0 * gc.N + 8.0 * Ch);
+  {
+    ProfileRange pr(K_CUFFT, fft_f, c->st);
+    CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)r, c->cbuf));
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->tl_cc, 0, 3 * Ch * sizeof(cufftComplex), c->st));
+  launch_tl_split(g, c->cbuf, c->tl_cc, 3, 1, (float)c->beta_v, (float)c->gamma,
+                  (float)(1.0 / (double)N), c->st);
+  {
+    ProfileRange pr(K_CUFFT, fft_c, c->st);
+    CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)c->tl_b));
+  }
+  // nested CG from x = 0: device scalars, one host read per iteration
+  const int nb = vector_blocks(n3c);
+  CUDA_TRY(c, cudaMemsetAsync(c->tl_x, 0, n3c * sizeof(float), c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->tl_r, c->tl_b, n3c * sizeof(float), cudaMemcpyDeviceToDevice,
+                              c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->tl_p, c->tl_b, n3c * sizeof(float), cudaMemcpyDeviceToDevice,
+                              c->st));
+  int cur = SLOT_TL_RR0, nxt = SLOT_TL_RR1;
+  launch_reduce(n3c, c->tl_b, nullptr, RED_SQ, c->partial, c->red_blocks, c->slots + cur, c->st);
+  TRY(check_launch(c, "nested cg"));
+  CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->slots + cur, sizeof(double), cudaMemcpyDeviceToHost,
+                              c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  double rr = c->hres[0];
+  const double stop2 = c->tl_rtol * c->tl_rtol * rr;
+  int it = 0;
+  while (it < c->opt.max_inner && rr > stop2 && std::isfinite(rr)) {
+    TRY(tl_reg_inv_sqrt(c, c->tl_p, c->tl_q));
+    launch_tl_outer(gc.N, c->tl_gm, c->tl_q, c->tl_Ap, c->st);
+    TRY(tl_reg_inv_sqrt(c, c->tl_Ap, c->tl_q));
+    launch_tl_finish_apply(n3c, c->tl_p, c->tl_q, c->tl_Ap, c->partial, nb,
+                           c->slots + SLOT_TL_PAP, c->st);
+    launch_tl_cg_step(n3c, c->slots + cur, c->slots + SLOT_TL_PAP, c->tl_x, c->tl_r, c->tl_p,
+                      c->tl_Ap, c->partial, nb, c->slots + nxt, c->st);
+    TRY(check_launch(c, "nested cg"));
+    CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->slots + SLOT_TL_RR0, 3 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    ++it;
+    const double pAp = c->hres[SLOT_TL_PAP - SLOT_TL_RR0];
+    if (!(pAp > 0.0) || !std::isfinite(pAp)) break;   // x, r unchanged by this step
+    rr = c->hres[nxt - SLOT_TL_RR0];
+    if (rr <= stop2) break;
+    launch_tl_cg_dir(n3c, c->slots + nxt, c->slots + cur, c->tl_r, c->tl_p, c->st);
+    std::swap(cur, nxt);
+  }
+  c->tl_iters += it;
+  {
+    ProfileRange pr(K_CUFFT, fft_c, c->st);
+    CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)c->tl_x, c->tl_cc));
+  }
+  launch_tl_merge(g, c->cbuf, c->tl_cc, c->cbuf2, (float)c->beta_v, (float)c->gamma,
+                  (float)(1.0 / (double)N), (float)(1.0 / (double)gc.N), c->st);
+  {
+    ProfileRange pr(K_CUFFT, 2 * fft_f, c->st);
+    CUFFT_TRY(c, cufftExecC2R(c->c2r, c->cbuf, (cufftReal*)z));
+    CUFFT_TRY(c, cufftExecC2R(c->c2r, c->cbuf2, (cufftReal*)Lz));
+  }
+  if (rz_slot >= 0)
+    launch_reduce(3 * N, r, z, RED_DOT, c->partial, c->red_blocks, c->slots + rz_slot, c->st);
+  return check_launch(c, "two-level preconditioner");
+}
+
 // z = M^-1 r with M = beta_v L (zero symbol set to one); <r, z> by Parseval into
 // slots[rz_slot] and the component means of r into slots[SLOT_MEAN..+2].
+// With options.precond = 1 the two-level preconditioner instead, with
+// beta_v L z in scr3.
 claire_status precondition(claire_ctx* c, int rz_slot) {
+  if (c->opt.precond == 1) return tl_precondition(c, c->r, c->z, c->scr3, rz_slot);
   const double fft_bytes = 3.0 * (4.0 * c->g.N + 8.0 * c->g.n1 * c->g.n2 * (c->g.n3 / 2 + 1));
   {
     ProfileRange pr(K_CUFFT, fft_bytes, c->st);
@@ -456,10 +646,17 @@ claire_status pcg_part_a(claire_ctx* c, int cur) {
   return CLAIRE_OK;
 }
 
+// beta_v L z for the recurrence of beta_v L s: r - mean(r) for the spectral
+// preconditioner, the field computed with z for the two-level one.
+const float* lz_source(const claire_ctx* c) { return c->opt.precond == 1 ? c->scr3 : c->r; }
+const double* lz_means(const claire_ctx* c) {
+  return c->slots + (c->opt.precond == 1 ? SLOT_ZERO : SLOT_MEAN);
+}
+
 claire_status pcg_part_b(claire_ctx* c, int cur, int nxt) {
   const int64_t N = N_of(c);
   TRY(precondition(c, nxt));
-  launch_s_update(N, c->slots + nxt, c->slots + cur, c->slots + SLOT_MEAN, 0, c->z, c->r, c->s,
+  launch_s_update(N, c->slots + nxt, c->slots + cur, lz_means(c), 0, c->z, lz_source(c), c->s,
                   c->hs, c->st);
   if (mixed(c))
     launch_reduce(3 * N, c->s, nullptr, RED_ABSMAX, c->partial, c->red_blocks,
@@ -479,7 +676,9 @@ void drop_graphs(claire_ctx* c) {
 // graph when options.graphs is set (captured on first use; the kernels inside
 // are counted per replay, not event-timed).
 claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
-  if (!c->opt.graphs)
+  // the nested CG of the two-level preconditioner reads its residual on the
+  // host, so part B is not captured then
+  if (!c->opt.graphs || (which == 1 && c->opt.precond == 1))
     return which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
   const int slot = 4 * (c->df == c->dbuf0 ? 0 : 1) + 2 * which + (cur == SLOT_RZ0 ? 0 : 1);
   if (!c->graph_exec[slot]) {
@@ -528,7 +727,7 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
   launch_lincomb(n3, -1.0f, c->grad, 0.0f, c->grad, c->r, c->st);    // r = -g
   int cur = SLOT_RZ0;
   TRY(precondition(c, cur));
-  launch_s_update(N, c->slots + cur, c->slots + cur, c->slots + SLOT_MEAN, 1, c->z, c->r, c->s,
+  launch_s_update(N, c->slots + cur, c->slots + cur, lz_means(c), 1, c->z, lz_source(c), c->s,
                   c->hs, c->st);
   if (mixed(c))
     launch_reduce(n3, c->s, nullptr, RED_ABSMAX, c->partial, c->red_blocks,
@@ -684,7 +883,15 @@ claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_sta
     double gg = 0.0;
     TRY(dot3(c, c->grad, c->grad, &gg));
     claire_status curv = CLAIRE_OK;
+    if (c->opt.precond == 1) {
+      // H0 at the current m(1); nested tolerance a tenth of the outer one (Sec. 2.6)
+      TRY(tl_update_image(c));
+      c->tl_rtol = c->opt.inner_rtol > 0.0 ? c->opt.inner_rtol : 0.1 * eta;
+      c->tl_iters = 0;
+    }
     TRY(pcg(c, eta * std::sqrt(gg), k, &curv));
+    k.inner += c->tl_iters;
+    c->tl_iters = 0;
     double gamma = 0.0;
     bool ok = false;
     TRY(armijo(c, k, &gamma, &ok));
@@ -728,6 +935,7 @@ claire_status finish_stats(claire_ctx* c, claire_stats* st, const Counters& k, f
   st->matvecs = k.matvecs;
   st->pde_solves = k.pde;
   st->linesearch_halvings = k.halvings;
+  st->inner_iters = k.inner;
   const int64_t N = N_of(c);
   double mis0 = 0.0;
   if (reduce(c, N, c->m0, c->m1, RED_SQDIFF, &mis0) == CLAIRE_OK && mis0 > 0.0) {
@@ -758,6 +966,9 @@ claire_status claire_default_options(claire_options* o) {
   o->forcing = 0;
   o->stream = nullptr;
   o->verbose = 0;
+  o->precond = 0;
+  o->max_inner = 50;
+  o->inner_rtol = 0.0;
   o->gnorm0 = 0.0;
   o->autotune = 0;
   o->graphs = 0;
@@ -773,6 +984,8 @@ claire_status claire_destroy(claire_ctx* c) {
     cufftDestroy(c->r2c);
     cufftDestroy(c->c2r);
   }
+  for (cufftHandle h : {c->tl_r2c1, c->tl_c2r1, c->tl_r2c3, c->tl_c2r3})
+    if (h) cufftDestroy(h);
   for (void* p : c->allocs) cudaFree(p);
   if (c->detf) cudaFree(c->detf);
   if (c->hres) cudaFreeHost(c->hres);
@@ -873,8 +1086,11 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
   if (!c || !o) return CLAIRE_EINVAL;
   if (o->precision < 0 || o->precision > 1 || o->hessian < 0 || o->hessian > 1 ||
       !(o->beta_w >= 0.0) || !(o->eps_opt > 0.0) || o->max_newton < 0 || o->max_pcg < 1 ||
-      o->forcing < 0 || o->forcing > 1)
+      o->forcing < 0 || o->forcing > 1 || o->precond < 0 || o->precond > 1 ||
+      (o->precond == 1 && o->max_inner < 1) || !std::isfinite(o->inner_rtol))
     return fail(c, CLAIRE_EINVAL, "invalid option value");
+  if (o->precond == 1 && (c->g.n1 % 4 || c->g.n2 % 4 || c->g.n3 % 4))
+    return fail(c, CLAIRE_EINVAL, "two-level preconditioner needs every n_i %% 4 == 0");
   if (o->hessian == 1)
     return fail(c, CLAIRE_EINVAL, "full-Newton Hessian is not available in this build");
   if (o->precision == 1 && !march_supported(c->nt))
@@ -902,7 +1118,10 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
   c->st = o->graphs ? c->own : c->user;
   CUFFT_TRY(c, cufftSetStream(c->r2c, c->st));
   CUFFT_TRY(c, cufftSetStream(c->c2r, c->st));
+  if (o->precond == 1) TRY(tl_setup(c));
+  TRY(tl_set_streams(c));
   c->have_eval = false;
+  c->tl_image = false;
   return CLAIRE_OK;
 }
 
@@ -1083,10 +1302,30 @@ claire_status claire_div8(claire_ctx* c, const float* w, float* dw) {
 
 claire_status claire_spectral(claire_ctx* c, int op, const float* in, float* out) {
   ENTER(c);
-  if (!c || !in || !out || op < 0 || op > 3) return CLAIRE_EINVAL;
+  if (!c || !in || !out || op < 0 || op > 4) return CLAIRE_EINVAL;
   if (op == CLAIRE_OP_NEAR_INC && !(c->opt.beta_w > 0.0))
     return fail(c, CLAIRE_EINVAL, "near-incompressible operator needs options.beta_w > 0");
   TRY(spectral(c, op, in, out, c->beta_v));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return CLAIRE_OK;
+}
+
+claire_status claire_precondition(claire_ctx* c, const float* r, float* z, int* inner_iters) {
+  ENTER(c);
+  if (!c || !r || !z) return CLAIRE_EINVAL;
+  if (inner_iters) *inner_iters = 0;
+  if (c->opt.precond == 0) {
+    TRY(spectral(c, CLAIRE_OP_REG_INV, r, z, c->beta_v));
+  } else {
+    if (!c->have_eval)
+      return fail(c, CLAIRE_EORDER, "precondition needs a prior objective_gradient");
+    TRY(tl_update_image(c));
+    c->tl_rtol = c->opt.inner_rtol > 0.0 ? c->opt.inner_rtol : 1e-3;
+    c->tl_iters = 0;
+    TRY(tl_precondition(c, r, z, c->scr3, -1));
+    if (inner_iters) *inner_iters = c->tl_iters;
+    c->tl_iters = 0;
+  }
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return CLAIRE_OK;
 }

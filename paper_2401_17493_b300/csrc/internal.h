@@ -18,7 +18,7 @@ namespace claire {
 // of CUDA events on the launch stream.
 enum KernelKind {
   K_TRACE, K_SL, K_ADJFAC, K_GRAD8, K_DIV8, K_SDOT, K_ACCUM, K_SPECTRAL, K_REDUCE, K_VECTOR,
-  K_DETF, K_CUFFT, K_COUNT
+  K_DETF, K_CUFFT, K_PRECOND, K_COUNT
 };
 const char* kernel_kind_name(int k);
 
@@ -110,6 +110,21 @@ void launch_axpy_h(int64_t n, float a, const float* x, float b, const __half* z,
                    cudaStream_t st);
 void launch_sqdiff_h(int64_t n, const __half* m, float a, const float* m1, double* partial,
                      int nblocks, double* out, cudaStream_t st);
+
+// Two-level preconditioner kernels (precond.cu).
+void launch_tl_split(const Grid& gf, cufftComplex* X, cufftComplex* C, int ncomp, int symbol,
+                     float alpha, float gamma, float scale, cudaStream_t st);
+void launch_tl_merge(const Grid& gf, cufftComplex* X, const cufftComplex* C, cufftComplex* X2,
+                     float alpha, float gamma, float sf, float sc, cudaStream_t st);
+void launch_tl_outer(int64_t n, const float* gm, const float* q, float* w, cudaStream_t st);
+void launch_tl_finish_apply(int64_t n, const float* p, const float* y, float* Ap,
+                            double* partial, int nblocks, double* pAp, cudaStream_t st);
+void launch_tl_cg_step(int64_t n, const double* rr, const double* pAp, float* x, float* r,
+                       const float* p, const float* Ap, double* partial, int nblocks,
+                       double* rr_new, cudaStream_t st);
+void launch_tl_cg_dir(int64_t n, const double* rr_new, const double* rr_old, const float* r,
+                      float* p, cudaStream_t st);
+void launch_tl_unscale_h(int64_t n, const __half* h, float inv, float* out, cudaStream_t st);
 
 enum ReduceMode {
   RED_DOT = 0, RED_SQDIFF = 1, RED_ABSMAX = 2, RED_SQ = 3, RED_MAX = 4, RED_MIN = 5, RED_SUM = 6

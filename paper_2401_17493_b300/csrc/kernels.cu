@@ -269,14 +269,15 @@ __global__ void __launch_bounds__(256) k_spectral(int n1, int n2, int n3, int64_
     const float kap = k1 * k1 + k2 * k2 + k3 * k3;
     const cufftComplex x0 = X[i], x1 = X[Nc + i], x2 = X[2 * Nc + i];
     cufftComplex y0, y1, y2;
-    if (op == 0 || op == 1) {
+    if (op == 0 || op == 1 || op == 4) {
       float sig = gamma == 1.0f ? kap : powf(kap, gamma);
       float f;
       if (op == 0) {
         f = sig * scale;                                  // L = (-Laplacian)^gamma
       } else {
         if (kap == 0.0f) sig = 1.0f;                      // zero symbol set to one
-        f = scale / (alpha * sig);                        // (alpha L)^-1
+        f = op == 1 ? scale / (alpha * sig)               // (alpha L)^-1
+                    : scale * rsqrtf(alpha * sig);        // (alpha L)^-1/2
       }
       y0 = make_cuComplex(x0.x * f, x0.y * f);
       y1 = make_cuComplex(x1.x * f, x1.y * f);
@@ -550,7 +551,7 @@ thread_local Profiler* tl_prof = nullptr;
 const char* kernel_kind_name(int k) {
   static const char* names[K_COUNT] = {"trace", "sl_step", "adjoint_factor", "grad8", "div8",
                                        "sdot_hist", "accum_hist", "spectral_diag", "reduce",
-                                       "vector", "detf", "cufft"};
+                                       "vector", "detf", "cufft", "precond"};
   return (k >= 0 && k < K_COUNT) ? names[k] : "?";
 }
 

@@ -1,0 +1,223 @@
+// Two-level zero-velocity preconditioner (Sec. 2.5.6): the spectral kernels
+// that split a residual into the part restricted to the grid of half the
+// resolution and the high-frequency remainder, merge the coarse solution back,
+// and the pointwise and vector kernels of the nested CG on the coarse grid.
+//
+// Fine half spectra are [3][n1][n2][n3/2+1] (cuFFT R2C layout), coarse ones
+// [3][n1/2][n2/2][n3/4+1].  A fine mode is "low" when |k_i| < n_i / 4 on every
+// axis (representable on the coarse grid without its Nyquist mode); F_L keeps
+// the low modes, F_H = I - F_L.  R^-1/2 has the symbol (alpha sigma(k))^-1/2
+// with sigma = |k|^(2 gamma) and the zero symbol set to one.
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace claire {
+namespace {
+
+struct ModeIdx {
+  int k1, k2, k3;
+  bool low;
+  int64_t ci;          // coarse half-spectrum index (valid when low)
+};
+
+__device__ __forceinline__ ModeIdx fine_mode(const Grid& g, int64_t i, int c1n, int c2n) {
+  const int nh = g.n3 / 2 + 1;
+  const int j3 = (int)(i % nh);
+  const int j2 = (int)((i / nh) % g.n2);
+  const int j1 = (int)(i / ((int64_t)nh * g.n2));
+  ModeIdx m;
+  m.k1 = j1 <= g.n1 / 2 ? j1 : j1 - g.n1;
+  m.k2 = j2 <= g.n2 / 2 ? j2 : j2 - g.n2;
+  m.k3 = j3;
+  m.low = abs(m.k1) < g.n1 / 4 && abs(m.k2) < g.n2 / 4 && m.k3 < g.n3 / 4;
+  const int c1 = m.k1 >= 0 ? m.k1 : m.k1 + c1n;
+  const int c2 = m.k2 >= 0 ? m.k2 : m.k2 + c2n;
+  const int ch = g.n3 / 4 + 1;                     // coarse half-spectrum length
+  m.ci = ((int64_t)c1 * c2n + c2) * ch + m.k3;
+  return m;
+}
+
+__device__ __forceinline__ float inv_sqrt_symbol(int k1, int k2, int k3, float alpha,
+                                                 float gamma) {
+  const float kap = (float)(k1 * k1 + k2 * k2 + k3 * k3);
+  float sig = gamma == 1.0f ? kap : powf(kap, gamma);
+  if (kap == 0.0f) sig = 1.0f;
+  return rsqrtf(alpha * sig);
+}
+
+// Split (ncomp fields): with symbol, X <- R^-1/2 X on the high modes and 0 on
+// the low ones, whose values R^-1/2 X * scale go to the coarse spectrum C;
+// without symbol, X is left alone and C gets X * scale on the low modes.  C
+// must be zeroed before (its coarse Nyquist modes are never written).
+__global__ void k_tl_split(Grid g, cufftComplex* __restrict__ X, cufftComplex* __restrict__ C,
+                           int ncomp, int symbol, float alpha, float gamma, float scale) {
+  const int64_t Nh = (int64_t)g.n1 * g.n2 * (g.n3 / 2 + 1);
+  const int64_t Ch = (int64_t)(g.n1 / 2) * (g.n2 / 2) * (g.n3 / 4 + 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nh) return;
+  const ModeIdx m = fine_mode(g, i, g.n1 / 2, g.n2 / 2);
+  const float f = symbol ? inv_sqrt_symbol(m.k1, m.k2, m.k3, alpha, gamma) : 1.0f;
+  for (int a = 0; a < ncomp; ++a) {
+    cufftComplex x = X[a * Nh + i];
+    x.x *= f;
+    x.y *= f;
+    if (m.low) {
+      C[a * Ch + m.ci] = make_cuComplex(x.x * scale, x.y * scale);
+      if (symbol) x = make_cuComplex(0.f, 0.f);
+    }
+    if (symbol) X[a * Nh + i] = x;
+  }
+}
+
+// Merge: U = low ? C * sc : X * sf (coarse solution prolonged, high part kept),
+// X <- R^-1/2 U (the preconditioned residual z) and X2 <- alpha sigma(k) R^-1/2 U
+// (alpha L z, zero mean).
+__global__ void k_tl_merge(Grid g, cufftComplex* __restrict__ X, const cufftComplex* __restrict__ C,
+                           cufftComplex* __restrict__ X2, float alpha, float gamma, float sf,
+                           float sc) {
+  const int64_t Nh = (int64_t)g.n1 * g.n2 * (g.n3 / 2 + 1);
+  const int64_t Ch = (int64_t)(g.n1 / 2) * (g.n2 / 2) * (g.n3 / 4 + 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nh) return;
+  const ModeIdx m = fine_mode(g, i, g.n1 / 2, g.n2 / 2);
+  const float f = inv_sqrt_symbol(m.k1, m.k2, m.k3, alpha, gamma);
+  const float kap = (float)(m.k1 * m.k1 + m.k2 * m.k2 + m.k3 * m.k3);
+  const float sig = gamma == 1.0f ? kap : powf(kap, gamma);   // 0 at k = 0
+  for (int a = 0; a < 3; ++a) {
+    cufftComplex u;
+    if (m.low) {
+      const cufftComplex cv = C[a * Ch + m.ci];
+      u = make_cuComplex(cv.x * sc, cv.y * sc);
+    } else {
+      const cufftComplex xv = X[a * Nh + i];
+      u = make_cuComplex(xv.x * sf, xv.y * sf);
+    }
+    const cufftComplex z = make_cuComplex(u.x * f, u.y * f);
+    X[a * Nh + i] = z;
+    X2[a * Nh + i] = make_cuComplex(alpha * sig * z.x, alpha * sig * z.y);
+  }
+}
+
+// w = gm (gm . q) pointwise (3 components, n nodes).
+__global__ void k_tl_outer(int64_t n, const float* __restrict__ gm, const float* __restrict__ q,
+                           float* __restrict__ w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float g0 = gm[i], g1 = gm[n + i], g2 = gm[2 * n + i];
+    const float d = g0 * q[i] + g1 * q[n + i] + g2 * q[2 * n + i];
+    w[i] = g0 * d;
+    w[n + i] = g1 * d;
+    w[2 * n + i] = g2 * d;
+  }
+}
+
+// Ap = p + y and this block's share of <p, Ap>.
+__global__ void __launch_bounds__(256) k_tl_finish_apply(int64_t n, const float* __restrict__ p,
+                                                         const float* __restrict__ y,
+                                                         float* __restrict__ Ap,
+                                                         double* __restrict__ partial) {
+  KahanF acc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = p[i] + y[i];
+    Ap[i] = a;
+    acc.add(p[i] * a);
+  }
+  const double b = block_sum(acc.value());
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
+// CG step: a = rr / pAp (0 when pAp <= 0 or not finite), x += a p, r -= a Ap,
+// and this block's share of ||r||^2.
+__global__ void __launch_bounds__(256) k_tl_cg_step(int64_t n, const double* __restrict__ rr,
+                                                    const double* __restrict__ pAp,
+                                                    float* __restrict__ x, float* __restrict__ r,
+                                                    const float* __restrict__ p,
+                                                    const float* __restrict__ Ap,
+                                                    double* __restrict__ partial) {
+  const double q = *pAp;
+  const float a = (q > 0.0 && isfinite(q)) ? (float)(*rr / q) : 0.0f;
+  KahanF acc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fmaf(a, p[i], x[i]);
+    const float rv = fmaf(-a, Ap[i], r[i]);
+    r[i] = rv;
+    acc.add(rv * rv);
+  }
+  const double b = block_sum(acc.value());
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
+// p = r + (rr_new / rr_old) p.
+__global__ void k_tl_cg_dir(int64_t n, const double* __restrict__ rr_new,
+                            const double* __restrict__ rr_old, const float* __restrict__ r,
+                            float* __restrict__ p) {
+  const float b = (float)(*rr_new / *rr_old);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(b, p[i], r[i]);
+}
+
+// FP16 field (scaled by sig) -> FP32 field / sig.
+__global__ void k_tl_unscale_h(int64_t n, const __half* __restrict__ h, float inv,
+                               float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = inv * __half2float(h[i]);
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+void launch_tl_split(const Grid& gf, cufftComplex* X, cufftComplex* C, int ncomp, int symbol,
+                     float alpha, float gamma, float scale, cudaStream_t st) {
+  const int64_t Nh = (int64_t)gf.n1 * gf.n2 * (gf.n3 / 2 + 1);
+  ProfileRange pr(K_PRECOND, (double)Nh * ncomp * (symbol ? 16 : 8) + (double)Nh * ncomp, st);
+  k_tl_split<<<nblk(Nh), 256, 0, st>>>(gf, X, C, ncomp, symbol, alpha, gamma, scale);
+}
+
+void launch_tl_merge(const Grid& gf, cufftComplex* X, const cufftComplex* C, cufftComplex* X2,
+                     float alpha, float gamma, float sf, float sc, cudaStream_t st) {
+  const int64_t Nh = (int64_t)gf.n1 * gf.n2 * (gf.n3 / 2 + 1);
+  ProfileRange pr(K_PRECOND, (double)Nh * 3 * 24, st);
+  k_tl_merge<<<nblk(Nh), 256, 0, st>>>(gf, X, C, X2, alpha, gamma, sf, sc);
+}
+
+void launch_tl_outer(int64_t n, const float* gm, const float* q, float* w, cudaStream_t st) {
+  ProfileRange pr(K_PRECOND, (double)n * 36, st);
+  k_tl_outer<<<vector_blocks(n), 256, 0, st>>>(n, gm, q, w);
+}
+
+void launch_tl_finish_apply(int64_t n, const float* p, const float* y, float* Ap,
+                            double* partial, int nblocks, double* pAp, cudaStream_t st) {
+  {
+    ProfileRange pr(K_PRECOND, (double)n * 12, st);
+    k_tl_finish_apply<<<nblocks, 256, 0, st>>>(n, p, y, Ap, partial);
+  }
+  launch_reduce_final(partial, nblocks, RED_SUM, pAp, st);
+}
+
+void launch_tl_cg_step(int64_t n, const double* rr, const double* pAp, float* x, float* r,
+                       const float* p, const float* Ap, double* partial, int nblocks,
+                       double* rr_new, cudaStream_t st) {
+  {
+    ProfileRange pr(K_PRECOND, (double)n * 24, st);
+    k_tl_cg_step<<<nblocks, 256, 0, st>>>(n, rr, pAp, x, r, p, Ap, partial);
+  }
+  launch_reduce_final(partial, nblocks, RED_SUM, rr_new, st);
+}
+
+void launch_tl_cg_dir(int64_t n, const double* rr_new, const double* rr_old, const float* r,
+                      float* p, cudaStream_t st) {
+  ProfileRange pr(K_PRECOND, (double)n * 12, st);
+  k_tl_cg_dir<<<vector_blocks(n), 256, 0, st>>>(n, rr_new, rr_old, r, p);
+}
+
+void launch_tl_unscale_h(int64_t n, const __half* h, float inv, float* out, cudaStream_t st) {
+  ProfileRange pr(K_PRECOND, (double)n * 6, st);
+  k_tl_unscale_h<<<vector_blocks(n), 256, 0, st>>>(n, h, inv, out);
+}
+
+}  // namespace claire
