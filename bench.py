@@ -4,7 +4,9 @@
 One step = one complete registration of the 256^3 brain-like phantom pair:
 beta_v continuation 1e-1 -> 1e-2 -> 1e-3 -> 1e-4 (Sec. 2.6), each level solved
 by inexact Gauss-Newton-Krylov to a relative gradient of 5e-2, nt = 4,
-H1-seminorm regularisation, FP32.  Inputs (m0, m1, v = 0) are resident in HBM
+H1-seminorm regularisation, FP32, PCG preconditioned with the two-level
+zero-velocity Hessian (the paper's default, Sec. 2.6; nested CG capped at 10
+iterations).  The same solve with the spectral preconditioner is reported beside it.  Inputs (m0, m1, v = 0) are resident in HBM
 when the timed region starts; the working set (~4 GB) is far larger than L2.
 
 Printed (rank 0, one JSON line): solve seconds per registration (value), plus
@@ -34,6 +36,8 @@ NT = 4
 EPS_OPT = 5e-2
 MAX_PCG = 200
 SEED = 2
+PRECOND = 1                # two-level zero-velocity preconditioner (Sec. 2.5.6, 2.6)
+MAX_INNER = 10             # nested CG cap per preconditioner application
 CPU_SAMPLE_N = 32          # oracle sample: the workload restricted to 32^3
 INTERP_FD = ("trace", "sl_step", "adjoint_factor", "grad8", "div8", "sdot_hist", "accum_hist")
 # DRAM traffic per voxel and launch measured by ncu for the kernels below (see
@@ -161,7 +165,7 @@ def run_batch(args, pairs):
     ctxs, vs = [], []
     for shape, m0, m1 in pairs:
         ctx = claire.Context(shape, nt=NT, beta_v=BATCH_BETA, eps_opt=EPS_OPT, max_pcg=MAX_PCG,
-                             graphs=1)
+                             graphs=1, precond=PRECOND, max_inner=MAX_INNER)
         ctx.set_images(torch.from_numpy(m0).cuda(), torch.from_numpy(m1).cuda())
         ctxs.append(ctx)
         vs.append(torch.zeros((3,) + shape, device="cuda"))
@@ -195,7 +199,8 @@ def run_batch(args, pairs):
             "all_converged": all(st.grad_rel <= EPS_OPT for st in bstats),
             "batched_equals_sequential": bool(same),
             "workload": "ellipsoid phantom pairs seeds 1000.., grids from {64^3, 96x112x80, "
-                        "128^3, 160x192x144, 192^3}, beta_v 5e-3, nt 4, rel-grad 5e-2"}
+                        "128^3, 160x192x144, 192^3}, beta_v 5e-3, nt 4, rel-grad 5e-2, "
+                        "two-level preconditioner"}
 
 
 def cpu_oracle_sample(m0, m1, n_full):
@@ -209,7 +214,9 @@ def cpu_oracle_sample(m0, m1, n_full):
     b = spectral.restrict(m1.astype(np.float64), (ns,) * 3)
     t0 = time.perf_counter()
     prob = reduced.Problem(a, b, nt=NT, beta_v=BETAS[0])
-    _, st, _ = solver.continuation(prob, BETAS, solver.Options(eps_opt=EPS_OPT, max_pcg=MAX_PCG))
+    _, st, _ = solver.continuation(prob, BETAS, solver.Options(
+        eps_opt=EPS_OPT, max_pcg=MAX_PCG, precond="two_level" if PRECOND else "spectral",
+        max_inner=MAX_INNER))
     dt = time.perf_counter() - t0
     scale = (n_full / ns) ** 3
     return dt * scale, dt, st
@@ -238,7 +245,8 @@ def run_reference(args, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{n}^3 ellipsoid phantom pair, continuation 1e-1..1e-4, nt 4",
+        "config": {"workload": f"{n}^3 ellipsoid phantom pair, continuation 1e-1..1e-4, nt 4, "
+                               "two-level preconditioner",
                    "sample": f"{CPU_SAMPLE_N}^3"},
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -265,7 +273,7 @@ def run_claire(args, world, rank, local):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     m0d, m1d = dev(m0), dev(m1)
     ctx = claire.Context(shape, nt=NT, beta_v=BETAS[0], eps_opt=EPS_OPT, max_newton=50,
-                         max_pcg=MAX_PCG)
+                         max_pcg=MAX_PCG, precond=PRECOND, max_inner=MAX_INNER)
     ctx.set_images(m0d, m1d)
     stream = torch.cuda.current_stream()
     v = torch.zeros((3,) + shape, device="cuda")
@@ -305,8 +313,33 @@ def run_claire(args, world, rank, local):
     s_per_solve = t_max / 1e3 / (args.steps * world)
     launches_per_step = sum(p["launches"] for k, p in prof.items() if k != "cufft") / args.steps
 
-    # mixed-precision form (FP16 field storage): same protocol, same accuracy criteria
+    # the same solve with the spectral preconditioner (beta_v L)^-1
     v_fp32 = v.clone()
+    ctx.set_options(precond=0)
+    vs_ = torch.zeros_like(v)
+    for _ in range(args.warmup):
+        vs_.zero_()
+        ctx.solve_continuation(BETAS, vs_)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    sstats = []
+    for _ in range(args.steps):
+        vs_.zero_()
+        _, sts = ctx.solve_continuation(BETAS, vs_)
+        sstats.append(sts.as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    spec_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    spectral_pc = {"value": spec_s, "unit": "s", "matvecs": sstats[-1]["matvecs"],
+                   "newton_iters": sstats[-1]["newton_iters"],
+                   "grad_rel": sstats[-1]["grad_rel"], "mismatch_rel": sstats[-1]["mismatch_rel"],
+                   "status": sstats[-1]["status"],
+                   "two_level_speedup": spec_s / (t_max / 1e3 / args.steps)}
+    ctx.set_options(precond=PRECOND)
+
+    # mixed-precision form (FP16 field storage): same protocol, same accuracy criteria
     ctx.set_options(precision=1)
     vm = torch.zeros_like(v)
     for _ in range(args.warmup):
@@ -390,10 +423,12 @@ def run_claire(args, world, rank, local):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"{n}^3 ellipsoid phantom pair (seed {SEED}), beta_v continuation "
-                               "1e-1..1e-4, rel-grad 5e-2 per level, nt 4, H1 seminorm, FP32",
+                               "1e-1..1e-4, rel-grad 5e-2 per level, nt 4, H1 seminorm, FP32, "
+                               "two-level zero-velocity preconditioner",
                    "l2": "working set ~%.1f GB > 126 MB L2" % (ctx.workspace_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "matvecs_per_s": matvecs_per_s,
+        "spectral_preconditioner": spectral_pc,
         "mixed": mixed,
         "batch": batch,
         "interp_fd_hbm_frac": interp_gbs / peak,
@@ -401,7 +436,7 @@ def run_claire(args, world, rank, local):
         "solve": {"newton_iters": st0["newton_iters"], "pcg_iters": st0["pcg_iters"],
                   "matvecs": st0["matvecs"], "pde_solves": st0["pde_solves"],
                   "grad_rel": st0["grad_rel"], "mismatch_rel": st0["mismatch_rel"],
-                  "status": st0["status"]},
+                  "inner_iters": st0["inner_iters"], "status": st0["status"]},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None if traffic is None else traffic * n ** 3,
