@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .reduced import evaluate, evaluate_objective, complete_gradient, hessian_matvec
+from .reduced import evaluate, evaluate_objective, complete_gradient, hessian_matvec, distance
 from .spectral import apply_reg_inverse
 from .precond import two_level_inverse, coarse_gradient
 
@@ -129,7 +129,7 @@ def gauss_newton(prob, v0=None, opts=None, gnorm0=None, stats=None):
             gnorm0 = float(np.max(np.abs(ev.g)))
     if stats.newton_iters == 0 and stats.J0 == 0.0:
         stats.J0 = ev.J
-    mis0 = 0.5 * prob.h3 * np.sum((prob.m0 - prob.m1) ** 2)
+    mis0 = distance(prob, prob.m0)
     k = 0
     while k < opts.max_newton:
         gnorm = float(np.max(np.abs(ev.g)))

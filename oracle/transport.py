@@ -108,8 +108,9 @@ def incremental_state_solve(m_hist, vt, v, nt, y=None):
     return mt
 
 
-def incremental_adjoint_solve(mt1, v, nt, lam_hist=None, vt=None, y=None):
-    """lam~^j, j = 0..nt, of eq. (incadj), solved backward from lam~^nt = -m~(1).
+def incremental_adjoint_solve(mt1, v, nt, lam_hist=None, vt=None, y=None, final=None):
+    """lam~^j, j = 0..nt, of eq. (incadj), solved backward from lam~^nt = -m~(1)
+    (or from the given final condition, e.g. the NCC one of the Appendix).
 
     Gauss-Newton (lam_hist is None): every lam term dropped (Sec. 2.5.5), so
     lam~ obeys the adjoint equation.  Full Newton: source q^j = div8(lam^j v~):
@@ -125,7 +126,7 @@ def incremental_adjoint_solve(mt1, v, nt, lam_hist=None, vt=None, y=None):
         vt = np.asarray(vt, dtype=np.float64)
         q = [div8(lam_j[None] * vt) for lam_j in lam_hist]
     lt = [None] * (nt + 1)
-    lt[nt] = -np.asarray(mt1, dtype=np.float64)
+    lt[nt] = -np.asarray(mt1, dtype=np.float64) if final is None else np.asarray(final, dtype=np.float64)
     for j in range(nt - 1, -1, -1):
         u_y = interp(lt[j + 1], y)
         f0 = u_y * D_y
