@@ -190,3 +190,54 @@ def continuation(prob, betas, opts=None, v0=None):
         stats.status = OK
         v, stats, ev = gauss_newton(prob, v, opts, gnorm0=gnorm0, stats=stats)
     return v, stats, ev
+
+
+def beta_search(solve, detf_bounds, eps_d=0.1, beta0=1.0, beta_min=1e-8, rtol=0.1,
+                max_bisect=10):
+    """Regularisation-parameter search with det-F bounds (Sec. 2.6, "Parameter
+    Selection"): eps_d < det grad y < 1/eps_d must hold (eq. ddgradbound).
+
+    Starting at beta0 the parameter drops by decades until the bound fails;
+    then a bisection runs between the last admissible value and the failing
+    one.  Every trial warm-starts from the previous trial's velocity.  Reading
+    C-17: the bisection takes the arithmetic midpoint and stops once the
+    bracket is narrower than rtol times its admissible end, or after
+    max_bisect steps; the result is the smallest admissible value found.
+
+    solve(beta, v0) -> v (v0 None: zero initial guess); detf_bounds(v) ->
+    (min det F1, max det F1).  Returns (beta*, v*, trials) with trials a list
+    of (beta, admissible, min det, max det); beta* is None when beta0 itself
+    violates the bound.
+    """
+    trials = []
+
+    def trial(beta, v0):
+        v = solve(beta, v0)
+        mn, mx = detf_bounds(v)
+        ok = eps_d < mn and mx < 1.0 / eps_d
+        trials.append((beta, ok, mn, mx))
+        return v, ok
+
+    beta, v = beta0, None
+    ok_beta, ok_v = None, None
+    while True:
+        v, ok = trial(beta, v)
+        if not ok:
+            break
+        ok_beta, ok_v = beta, v
+        if beta / 10.0 < beta_min * (1.0 - 1e-9):
+            return ok_beta, ok_v, trials
+        beta /= 10.0
+    if ok_beta is None:
+        return None, None, trials
+    lo, hi = beta, ok_beta
+    for _ in range(max_bisect):
+        if hi - lo <= rtol * hi:
+            break
+        mid = 0.5 * (lo + hi)
+        v, ok = trial(mid, v)
+        if ok:
+            hi, ok_v = mid, v
+        else:
+            lo = mid
+    return hi, ok_v, trials

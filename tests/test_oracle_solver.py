@@ -71,3 +71,64 @@ def test_gauss_newton_reaches_the_relative_gradient_tolerance():
     assert st.grad_rel <= 5e-2
     # each Newton iteration costs 2 PDE solves per matvec + line-search state solves + adjoint
     assert st.pde_solves >= 2 + 2 * st.matvecs + 2 * st.newton_iters
+
+
+def test_beta_search_sequence_on_a_known_threshold():
+    """Brute force of the search rule with a stand-in solver: admissible iff
+    beta >= 3.7e-3 (decades 1 .. 1e-2 pass, 1e-3 fails, then bisection)."""
+    calls = []
+
+    def solve(beta, v0):
+        calls.append((beta, v0))
+        return beta                                  # the 'velocity' carries beta
+
+    def bounds(v):
+        return (0.5, 1.5) if v >= 3.7e-3 else (0.05, 3.0)
+
+    beta, v, trials = S.beta_search(solve, bounds, eps_d=0.1, rtol=0.1)
+    seq = [t[0] for t in trials]
+    expect = [1.0, 0.1, 0.01, 1e-3]
+    lo, hi = 1e-3, 1e-2
+    while hi - lo > 0.1 * hi:
+        mid = 0.5 * (lo + hi)
+        expect.append(mid)
+        if mid >= 3.7e-3:
+            hi = mid
+        else:
+            lo = mid
+    assert np.allclose(seq, expect)
+    assert beta == hi and v == hi and 3.7e-3 <= beta < 3.7e-3 / 0.9
+    # warm starts: each trial starts from the previous trial's velocity
+    assert calls[0][1] is None and all(calls[i][1] == calls[i - 1][0] for i in range(1, len(calls)))
+
+
+def test_beta_search_edge_cases():
+    solve = lambda b, v0: b
+    beta, _, trials = S.beta_search(solve, lambda v: (0.01, 2.0), eps_d=0.1)
+    assert beta is None and len(trials) == 1                # beta0 already violates
+    beta, _, trials = S.beta_search(solve, lambda v: (0.9, 1.1), eps_d=0.1, beta_min=1e-3)
+    assert abs(beta - 1e-3) < 1e-15 and len(trials) == 4    # never violated down to beta_min
+    beta, _, trials = S.beta_search(solve, lambda v: (0.5, 20.0) if v < 0.05 else (0.5, 2.0),
+                                    eps_d=0.1)
+    assert trials[2][1] is False and 0.05 <= beta <= 0.1      # upper bound 1/eps_d checked
+
+
+def test_beta_search_on_a_registration_keeps_det_f_in_bounds():
+    from oracle import defgrad as D
+    m0, m1, v = synth.blob_pair((16, 16, 16), seed=5, kmax=2, max_disp_voxels=2.5)
+    p = R.Problem(m0, m1, nt=4, beta_v=1.0)
+    gnorm0 = float(np.max(np.abs(R.gradient_at_zero(p))))
+
+    def solve(beta, v0):
+        p.beta_v = beta
+        vs, _, _ = S.gauss_newton(p, v0, S.Options(eps_opt=5e-2), gnorm0=gnorm0)
+        return vs
+
+    def bounds(v):
+        _, (mn, mx, _) = D.det_deformation_gradient(v, 4)
+        return mn, mx
+
+    beta, vb, trials = S.beta_search(solve, bounds, eps_d=0.5, rtol=0.2, max_bisect=4)
+    assert beta is not None and any(not t[1] for t in trials)
+    mn, mx = bounds(vb)
+    assert 0.5 < mn and mx < 2.0
