@@ -47,7 +47,11 @@ typedef enum {
 typedef struct {
   int precision;        /* 0: FP32 storage (default). 1: mixed (16-bit field storage,
                            FP32 math and coordinates, FP64 reductions)               */
-  int hessian;          /* 0: Gauss-Newton (default, Sec. 2.5.5). 1: full Newton     */
+  int hessian;          /* 0: Gauss-Newton (default, Sec. 2.5.5). 1: full Newton (eq.
+                           matvec with the lam terms: sources div(lam^j vt) in the
+                           incremental adjoint and sum_j w_j lam^j grad m~^j); needs
+                           precision 0 and (nt + 2) N more floats; PCG ends on
+                           negative curvature as in Sec. 2.5.5                      */
   double beta_w;        /* divergence-penalty weight of the near-incompressible model
                            (Appendix); 0 = plain H1 seminorm (default)             */
   double eps_opt;       /* relative gradient tolerance, default 5e-2 (Sec. 2.6)      */
@@ -71,6 +75,9 @@ typedef struct {
   int max_inner;        /* nested CG iteration cap of precond 1 (default 50)          */
   double inner_rtol;    /* > 0: fixed relative tolerance of the nested CG; <= 0: one
                            tenth of the outer PCG's relative tolerance (Sec. 2.6)    */
+  int distance;         /* 0: 1/2 ||m(1) - m1||^2 (default, eq. varopt-claire).  1: NCC,
+                           1 - <m(1), m1>^2 / (||m1||^2 ||m(1)||^2) (Appendix), which
+                           changes lam(1) and lam~(1); needs precision 0             */
 } claire_options;
 
 typedef struct {
@@ -166,6 +173,24 @@ claire_status claire_div8(claire_ctx* ctx, const float* w, float* div_w);
 enum { CLAIRE_OP_L = 0, CLAIRE_OP_REG_INV = 1, CLAIRE_OP_LERAY_PAR = 2, CLAIRE_OP_NEAR_INC = 3,
        CLAIRE_OP_REG_INV_SQRT = 4 };
 claire_status claire_spectral(claire_ctx* ctx, int op, const float* in, float* out);
+
+/* Regularisation-parameter search with det F bounds (Sec. 2.6, "Parameter
+ * Selection", eq. ddgradbound): starting at beta0, beta_v drops by decades
+ * until eps_d < min det F1 and max det F1 < 1/eps_d fails (or beta_min is
+ * reached), then bisects between the last admissible and the failing value
+ * (arithmetic midpoint; stops when the bracket is narrower than rtol times its
+ * admissible end or after max_bisect steps).  Each trial is a Gauss-Newton
+ * solve (options as set) warm-started from the previous trial.  v_inout
+ * (device [3][N]) is the initial guess on entry and the velocity of *beta_out
+ * (the smallest admissible value found) on return; *beta_out = 0 when beta0
+ * already violates the bound (v_inout then holds that trial's velocity).
+ * Up to max_trials (beta, min det F1, max det F1) triples go to the host
+ * arrays; *ntrials (may be NULL) receives the number of trials.  stats (may
+ * be NULL) sums all trials.  0 < eps_d < 1, beta0, beta_min, rtol > 0. */
+claire_status claire_beta_search(claire_ctx* ctx, double eps_d, double beta0, double beta_min,
+                                 double rtol, int max_bisect, float* v_inout, double* beta_out,
+                                 double* trial_beta, double* trial_detmin, double* trial_detmax,
+                                 int max_trials, int* ntrials, claire_stats* stats);
 
 /* z = M^-1 r (device [3][N]) with the preconditioner of options.precond
  * (Sec. 2.5.6) at the image m(1) of the last claire_objective_gradient

@@ -27,7 +27,7 @@ EXPORTED = [
     "claire_transport_noalloc", "claire_autotune", "claire_solve_batch",
     "claire_conv3d_forward", "claire_conv3d_flip_weights", "claire_conv3d_wgrad",
     "claire_unet_op", "claire_unet_bias_grad", "claire_unet_pack", "claire_unet_mse",
-    "claire_unet_adam", "claire_resample", "claire_precondition",
+    "claire_unet_adam", "claire_resample", "claire_precondition", "claire_beta_search",
 ]
 
 
@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("verbose", ctypes.c_int),
                 ("gnorm0", ctypes.c_double), ("autotune", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("precond", ctypes.c_int),
-                ("max_inner", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
+                ("max_inner", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("distance", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +95,8 @@ def load_library(path=LIB_PATH):
         "claire_objective_gradient": ([P, P, ctypes.POINTER(D), P], I),
         "claire_hessian_matvec": ([P, P, P], I),
         "claire_precondition": ([P, P, P, ctypes.POINTER(I)], I),
+        "claire_beta_search": ([P, D, D, D, D, I, P, ctypes.POINTER(D), P, P, P, I,
+                                ctypes.POINTER(I), ctypes.POINTER(Stats)], I),
         "claire_solve": ([P, P, ctypes.POINTER(Stats)], I),
         "claire_solve_continuation": ([P, ctypes.POINTER(D), I, P, ctypes.POINTER(Stats)], I),
         "claire_solve_host": ([P, P, P, ctypes.POINTER(D), I, P, ctypes.POINTER(Stats)], I),
@@ -293,6 +296,28 @@ class Context:
         self._check(self.lib.claire_precondition(self.h, _ptr(r, self.vshape, "r"),
                                                  _ptr(out, self.vshape, "z"), ctypes.byref(its)))
         return out, its.value
+
+    def beta_search(self, v=None, eps_d=0.1, beta0=1.0, beta_min=1e-8, rtol=0.1, max_bisect=10,
+                    max_trials=64):
+        """Regularisation-parameter search with det F bounds (Sec. 2.6).
+
+        Returns (beta*, v, trials, stats); trials is a list of (beta, min det F1,
+        max det F1); beta* is 0.0 when beta0 already violates the bound."""
+        import torch
+        v = torch.zeros(self.vshape, device="cuda") if v is None else v
+        tb = (ctypes.c_double * max_trials)()
+        tmn = (ctypes.c_double * max_trials)()
+        tmx = (ctypes.c_double * max_trials)()
+        nt = ctypes.c_int(0)
+        beta = ctypes.c_double(0.0)
+        st = Stats()
+        r = self.lib.claire_beta_search(self.h, float(eps_d), float(beta0), float(beta_min),
+                                        float(rtol), int(max_bisect), _ptr(v, self.vshape, "v"),
+                                        ctypes.byref(beta), tb, tmn, tmx, int(max_trials),
+                                        ctypes.byref(nt), ctypes.byref(st))
+        self._solve_status(r)
+        trials = [(tb[i], tmn[i], tmx[i]) for i in range(min(nt.value, max_trials))]
+        return beta.value, v, trials, st
 
     def _solve_status(self, st):
         if st not in (OK, ENOTCONV, ELINESEARCH):

@@ -38,6 +38,10 @@ struct claire_ctx {
   float *shist = nullptr, *pp0 = nullptr, *pp1 = nullptr, *lthist = nullptr;
   float *vt = nullptr, *r = nullptr, *z = nullptr, *s = nullptr, *Hs = nullptr;
   float* hs = nullptr;          // beta_v L s, carried by recurrence inside PCG
+  // full Newton (options.hessian = 1), allocated on first use: the incremental
+  // state history m~^j and e(x) = (h_t/2)(1 + h_t div v(x))
+  float *mthist = nullptr, *ef = nullptr;
+  float* vbest = nullptr;       // velocity of the last admissible beta (claire_beta_search)
   double* slots = nullptr;      // device FP64 scalars of PCG (see pcg())
   int* dflag = nullptr;         // device flag: negative curvature / non-finite PCG scalar
   double* hslots = nullptr;     // pinned host mirror of slots + flag
@@ -54,6 +58,9 @@ struct claire_ctx {
   float* detf = nullptr;
   bool have_eval = false;
   double J = 0.0, dist = 0.0;
+  // NCC distance (options.distance = 1): <m1, m(1)>, ||m1||^2, ||m(1)||^2 (L2, with h^3)
+  // of the last objective evaluation
+  double ncc_a = 0.0, ncc_b = 0.0, ncc_c = 0.0;
   std::string err;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   Profiler prof;
@@ -209,7 +216,8 @@ bool mixed(const claire_ctx* c) { return c->opt.precision == 1; }
 
 // Slots of the device-side FP64 scalars.
 enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4, SLOT_VMAX = 8,
-       SLOT_TL_RR0 = 9, SLOT_TL_RR1 = 10, SLOT_TL_PAP = 11, SLOT_ZERO = 12 /* ..14 */ };
+       SLOT_TL_RR0 = 9, SLOT_TL_RR1 = 10, SLOT_TL_PAP = 11, SLOT_ZERO = 12 /* ..14 */,
+       SLOT_NCC_AL = 15, SLOT_NCC_GA = 16, NSLOTS = 24 };
 
 // Power-of-two scale that maps max(|m0|, |m1|) into (1/2, 1] (FP16 state range).
 claire_status image_scale(claire_ctx* c) {
@@ -240,6 +248,15 @@ claire_status accumulate(claire_ctx* c, const float* lhist, const __half* lh, co
     launch_accum_hist(c->g, lhist, c->mhist, c->nt, base, base_coef, out, c->st, dotv, partial);
   }
   return check_launch(c, "accumulate");
+}
+
+// Full Newton (options.hessian = 1): out += sum_j w_j lam^j grad m~^j, the term of
+// eq. (matvec) that Gauss-Newton drops; with partial, per-block shares of
+// <dotv, out>.  No-op for Gauss-Newton.
+claire_status accumulate_newton(claire_ctx* c, float* out, const float* dotv, double* partial) {
+  if (c->opt.hessian != 1) return CLAIRE_OK;
+  launch_accum_hist(c->g, c->lhist, c->mthist, c->nt, out, 1.0f, out, c->st, dotv, partial);
+  return check_launch(c, "full-Newton accumulate");
 }
 
 // m^0 = m0, m^{j+1}(x) = m^j(x + d_f(x))  (eq. transport, homogeneous SL steps)
@@ -273,12 +290,22 @@ claire_status objective(claire_ctx* c, const float* v, double* J) {
                                 c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     sq = c->hres[0];
+  } else if (c->opt.distance == 1) {           // NCC (Appendix)
+    const float* m = c->mhist + c->nt * N;
+    double a = 0.0, b = 0.0, cc = 0.0;
+    TRY(reduce(c, N, m, c->m1, RED_DOT, &a));
+    TRY(reduce(c, N, c->m1, nullptr, RED_SQ, &b));
+    TRY(reduce(c, N, m, nullptr, RED_SQ, &cc));
+    c->ncc_a = h3 * a; c->ncc_b = h3 * b; c->ncc_c = h3 * cc;
+    if (!(c->ncc_b > 0.0) || !(c->ncc_c > 0.0))
+      return fail(c, CLAIRE_ENONFINITE, "NCC distance of a zero image");
   } else {
     TRY(reduce(c, N, c->mhist + c->nt * N, c->m1, RED_SQDIFF, &sq));
   }
   TRY(spectral(c, CLAIRE_OP_L, v, c->Lv, 1.0));
   TRY(dot3(c, v, c->Lv, &vLv));
-  c->dist = 0.5 * h3 * sq;
+  c->dist = c->opt.distance == 1 ? 1.0 - c->ncc_a * c->ncc_a / (c->ncc_b * c->ncc_c)
+                                  : 0.5 * h3 * sq;
   *J = c->dist + 0.5 * c->beta_v * h3 * vLv;
   if (!std::isfinite(*J)) return fail(c, CLAIRE_ENONFINITE, "objective is not finite (%g)", *J);
   return CLAIRE_OK;
@@ -292,13 +319,23 @@ claire_status adjoint_and_gradient(claire_ctx* c) {
   launch_trace(g, c->v, nullptr, c->db, ht_of(c), c->st);
   launch_div8(g, c->v, c->D, c->st);
   launch_adjoint_factor(g, c->D, c->db, ht_of(c), c->cf, c->st);
+  if (c->opt.hessian == 1) {
+    const float ht = ht_of(c);
+    launch_affine(N, 0.5f * ht * ht, c->D, 0.5f * ht, c->ef, c->st);
+  }
   if (mixed(c)) {                                  // FP16 history of sig_m lam
     launch_axpy_h(N, c->sig_m, c->m1, -1.0f, c->mh + c->nt * N, c->lh + c->nt * N, c->st);
     for (int j = c->nt - 1; j >= 0; --j)
       launch_sl_h(g, c->lh + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lh + j * N,
                   c->st);
   } else {
-    launch_lincomb(N, 1.0f, c->m1, -1.0f, c->mhist + c->nt * N, c->lhist + c->nt * N, c->st);
+    if (c->opt.distance == 1) {                  // lam(1) = -d dist_NCC / d m(1)
+      const double a = c->ncc_a, b = c->ncc_b, cc = c->ncc_c;
+      launch_lincomb(N, (float)(2.0 * a / (b * cc)), c->m1, (float)(-2.0 * a * a / (b * cc * cc)),
+                     c->mhist + c->nt * N, c->lhist + c->nt * N, c->st);
+    } else {
+      launch_lincomb(N, 1.0f, c->m1, -1.0f, c->mhist + c->nt * N, c->lhist + c->nt * N, c->st);
+    }
     for (int j = c->nt - 1; j >= 0; --j)
       launch_sl(g, c->lhist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lhist + j * N,
                 c->st);
@@ -350,12 +387,14 @@ claire_status matvec(claire_ctx* c, const float* vt, float* Hvt) {
   TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
   if (c->opt.beta_w > 0.0) {
     TRY(accumulate(c, c->lthist, c->lth, nullptr, 0.0f, Hvt, vmax, nullptr, nullptr));
+    TRY(accumulate_newton(c, Hvt, nullptr, nullptr));
     TRY(project_data_term(c, Hvt));
     TRY(spectral(c, CLAIRE_OP_L, vt, c->scr3, 1.0));
     launch_axpby(3 * N, (float)c->beta_v, c->scr3, 1.0f, Hvt, c->st);
   } else {
     TRY(accumulate(c, c->lthist, c->lth, c->scr3, (float)c->beta_v, Hvt, vmax, nullptr,
                    nullptr));
+    TRY(accumulate_newton(c, Hvt, nullptr, nullptr));
   }
   return check_launch(c, "matvec accumulate");
 }
@@ -392,11 +431,12 @@ claire_status matvec_transport(claire_ctx* c, const float* vt) {
                   c->st);
     return check_launch(c, "matvec transport");
   }
+  const bool newton = c->opt.hessian == 1;
   launch_sdot_hist(g, c->mhist, nt, vt, -0.5f * ht, c->shist, c->st);
   const float* src = c->shist;                       // w^0
   for (int j = 0; j < nt; ++j) {
-    if (j < nt - 1) {
-      float* dst = (j % 2 == 0) ? c->pp0 : c->pp1;
+    if (j < nt - 1) {                                // full Newton keeps every w^j
+      float* dst = newton ? c->mthist + (j + 1) * N : ((j % 2 == 0) ? c->pp0 : c->pp1);
       launch_sl(g, src, c->df, nullptr, 1.0f, c->shist + (j + 1) * N, -ht, dst, c->st);
       src = dst;
     } else {                                         // lam~(1) = -m~(1)
@@ -404,9 +444,41 @@ claire_status matvec_transport(claire_ctx* c, const float* vt) {
                 c->lthist + nt * N, c->st);
     }
   }
-  for (int j = nt - 1; j >= 0; --j)
-    launch_sl(g, c->lthist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f, c->lthist + j * N,
+  // Full Newton (eq. incadj with the lam terms): m~^0 = 0, m~^j = w^j + (h_t/2) s^j,
+  // m~^nt = -(lthist^nt, which holds -m~(1) here)
+  if (newton) {
+    CUDA_TRY(c, cudaMemsetAsync(c->mthist, 0, N * sizeof(float), c->st));
+    for (int j = 1; j < nt; ++j)
+      launch_lincomb(N, 1.0f, c->mthist + j * N, 0.5f * ht, c->shist + j * N,
+                     c->mthist + j * N, c->st);
+    launch_lincomb(N, -1.0f, c->lthist + nt * N, 0.0f, c->lthist + nt * N, c->mthist + nt * N,
+                   c->st);
+  }
+  if (c->opt.distance == 1) {                    // NCC: lam~(1) = -(d^2 dist)[m~(1)]
+    const float* m = c->mhist + nt * N;
+    float* lt = c->lthist + nt * N;
+    launch_reduce(N, c->m1, lt, RED_DOT, c->partial, c->red_blocks, c->slots + SLOT_NCC_AL,
+                  c->st);
+    launch_reduce(N, m, lt, RED_DOT, c->partial, c->red_blocks, c->slots + SLOT_NCC_GA, c->st);
+    launch_ncc_final(N, c->m1, m, lt, c->slots + SLOT_NCC_AL, c->slots + SLOT_NCC_GA, c->ncc_a,
+                     c->ncc_b, c->ncc_c, (double)g.h1 * g.h2 * g.h3, c->st);
+  }
+  if (!newton) {
+    for (int j = nt - 1; j >= 0; --j)
+      launch_sl(g, c->lthist + (j + 1) * N, c->db, c->cf, 1.0f, nullptr, 0.0f,
+                c->lthist + j * N, c->st);
+    return check_launch(c, "matvec transport");
+  }
+  // sources q^j = div8(lam^j vt) (in shist, s no longer needed);
+  // lam~^j(x) = c(x) lam~^{j+1}(y) + e(x) q^{j+1}(y) + (h_t/2) q^j(x), the RK2 step
+  // of the paper with e = (h_t/2)(1 + h_t div v), as two SL launches.
+  for (int j = 0; j <= nt; ++j) launch_div8_prod(g, c->lhist + j * N, vt, c->shist + j * N, c->st);
+  for (int j = nt - 1; j >= 0; --j) {
+    launch_sl(g, c->lthist + (j + 1) * N, c->db, c->cf, 1.0f, c->shist + j * N, 0.5f * ht,
+              c->pp0, c->st);
+    launch_sl(g, c->shist + (j + 1) * N, c->db, c->ef, 1.0f, c->pp0, 1.0f, c->lthist + j * N,
               c->st);
+  }
   return check_launch(c, "matvec transport");
 }
 
@@ -487,6 +559,12 @@ claire_status tl_update_image(claire_ctx* c) {
     CUFFT_TRY(c, cufftExecC2R(c->tl_c2r1, c->tl_cc, (cufftReal*)c->tl_mc));
   }
   launch_grad8(c->gc, c->tl_mc, c->tl_gm, c->st);
+  if (c->opt.distance == 1) {
+    // NCC: the pointwise part of d^2 dist / d m(1)^2 is 2 a^2 / (b c^2) times the identity
+    const double w = 2.0 * c->ncc_a * c->ncc_a / (c->ncc_b * c->ncc_c * c->ncc_c);
+    const int64_t n3c = 3 * c->gc.N;
+    launch_lincomb(n3c, (float)std::sqrt(w), c->tl_gm, 0.0f, c->tl_gm, c->tl_gm, c->st);
+  }
   TRY(check_launch(c, "two-level image"));
   c->tl_image = true;
   return CLAIRE_OK;
@@ -626,11 +704,16 @@ claire_status pcg_part_a(claire_ctx* c, int cur) {
   const Grid& g = c->g;
   const double* vmax = mixed(c) ? c->slots + SLOT_VMAX : nullptr;
   TRY(matvec_transport(c, c->s));
+  const bool newton = c->opt.hessian == 1;
   if (c->opt.beta_w <= 0.0 && march_supported(c->nt)) {
-    TRY(accumulate(c, c->lthist, c->lth, c->hs, 1.0f, c->Hs, vmax, c->s, c->partial));
+    // <s, H s> fused into the last accumulation
+    TRY(accumulate(c, c->lthist, c->lth, c->hs, 1.0f, c->Hs, vmax, newton ? nullptr : c->s,
+                   newton ? nullptr : c->partial));
+    TRY(accumulate_newton(c, c->Hs, c->s, c->partial));
     launch_reduce_final(c->partial, march_blocks(g), RED_SUM, c->slots + SLOT_SHS, c->st);
   } else {
     TRY(accumulate(c, c->lthist, c->lth, nullptr, 0.0f, c->Hs, vmax, nullptr, nullptr));
+    TRY(accumulate_newton(c, c->Hs, nullptr, nullptr));
     TRY(project_data_term(c, c->Hs));
     launch_axpby(n3, 1.0f, c->hs, 1.0f, c->Hs, c->st);
     launch_reduce(n3, c->s, c->Hs, RED_DOT, c->partial, c->red_blocks, c->slots + SLOT_SHS,
@@ -641,7 +724,7 @@ claire_status pcg_part_a(claire_ctx* c, int cur) {
                     c->partial, vb, c->dflag, c->st);
   launch_reduce_final(c->partial, vb, RED_SUM, c->slots + SLOT_RR, c->st);
   TRY(check_launch(c, "pcg update"));
-  CUDA_TRY(c, cudaMemcpyAsync(c->hslots, c->slots, 16 * sizeof(double) + sizeof(int),
+  CUDA_TRY(c, cudaMemcpyAsync(c->hslots, c->slots, NSLOTS * sizeof(double) + sizeof(int),
                               cudaMemcpyDeviceToHost, c->st));
   return CLAIRE_OK;
 }
@@ -739,7 +822,7 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
     k.pde += 2;
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     const double sHs = c->hslots[SLOT_SHS], rr = c->hslots[SLOT_RR];
-    const int flag = *(const int*)(c->hslots + 16);
+    const int flag = *(const int*)(c->hslots + NSLOTS);
     if (flag) {
       if (!std::isfinite(sHs) || !std::isfinite(c->hslots[cur]))
         return fail(c, CLAIRE_ENONFINITE, "PCG scalar not finite");
@@ -851,6 +934,8 @@ claire_status autotune(claire_ctx* c) {
 
 // Algorithm 1 from the iterate in c->v; gnorm0 > 0 fixes the relative-gradient
 // denominator (reading C-10), else ||g(v = 0)||_inf is computed first.
+claire_status detf_stats(claire_ctx* c, const float* v, double* mmm, float* det_out);
+
 claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_stats* out) {
   const int64_t n3 = 3 * N_of(c);
   double vmax = 0.0;
@@ -938,7 +1023,15 @@ claire_status finish_stats(claire_ctx* c, claire_stats* st, const Counters& k, f
   st->inner_iters = k.inner;
   const int64_t N = N_of(c);
   double mis0 = 0.0;
-  if (reduce(c, N, c->m0, c->m1, RED_SQDIFF, &mis0) == CLAIRE_OK && mis0 > 0.0) {
+  if (c->opt.distance == 1) {                      // NCC distance of the template
+    double a = 0.0, b = 0.0, cc = 0.0;
+    if (reduce(c, N, c->m0, c->m1, RED_DOT, &a) == CLAIRE_OK &&
+        reduce(c, N, c->m1, nullptr, RED_SQ, &b) == CLAIRE_OK &&
+        reduce(c, N, c->m0, nullptr, RED_SQ, &cc) == CLAIRE_OK && b > 0.0 && cc > 0.0) {
+      mis0 = 1.0 - a * a / (b * cc);
+      if (mis0 > 0.0) st->mismatch_rel = c->dist / mis0;
+    }
+  } else if (reduce(c, N, c->m0, c->m1, RED_SQDIFF, &mis0) == CLAIRE_OK && mis0 > 0.0) {
     const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
     st->mismatch_rel = c->dist / (0.5 * h3 * mis0);
   }
@@ -969,6 +1062,7 @@ claire_status claire_default_options(claire_options* o) {
   o->precond = 0;
   o->max_inner = 50;
   o->inner_rtol = 0.0;
+  o->distance = 0;
   o->gnorm0 = 0.0;
   o->autotune = 0;
   o->graphs = 0;
@@ -1038,20 +1132,20 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
     pb = std::max(pb, vector_blocks(3 * N / 4));
     c->partial_blocks = pb;
     void* p = nullptr;
-    if (cudaMalloc(&p, (size_t)(pb + 8 + 16 + 4) * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&p, (size_t)(pb + 8 + NSLOTS + 4) * sizeof(double)) != cudaSuccess) {
       s = CLAIRE_ENOMEM;
     } else {
       c->allocs.push_back(p);
       c->partial = (double*)p;
       c->dres = c->partial + pb;
       c->slots = c->dres + 8;
-      c->dflag = (int*)(c->slots + 16);
-      c->bytes += (size_t)(pb + 28) * sizeof(double);
+      c->dflag = (int*)(c->slots + NSLOTS);
+      c->bytes += (size_t)(pb + 8 + NSLOTS + 4) * sizeof(double);
     }
   }
   if (s == CLAIRE_OK && cudaMallocHost(&c->hres, 8 * sizeof(double)) != cudaSuccess)
     s = CLAIRE_ENOMEM;
-  if (s == CLAIRE_OK && cudaMallocHost(&c->hslots, 20 * sizeof(double)) != cudaSuccess)
+  if (s == CLAIRE_OK && cudaMallocHost(&c->hslots, (NSLOTS + 4) * sizeof(double)) != cudaSuccess)
     s = CLAIRE_ENOMEM;
   if (s == CLAIRE_OK) {
     int n[3] = {nx, ny, nz};
@@ -1087,12 +1181,19 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
   if (o->precision < 0 || o->precision > 1 || o->hessian < 0 || o->hessian > 1 ||
       !(o->beta_w >= 0.0) || !(o->eps_opt > 0.0) || o->max_newton < 0 || o->max_pcg < 1 ||
       o->forcing < 0 || o->forcing > 1 || o->precond < 0 || o->precond > 1 ||
-      (o->precond == 1 && o->max_inner < 1) || !std::isfinite(o->inner_rtol))
+      (o->precond == 1 && o->max_inner < 1) || !std::isfinite(o->inner_rtol) ||
+      o->distance < 0 || o->distance > 1)
     return fail(c, CLAIRE_EINVAL, "invalid option value");
+  if (o->distance == 1 && o->precision != 0)
+    return fail(c, CLAIRE_EINVAL, "the NCC distance needs FP32 storage (precision 0)");
   if (o->precond == 1 && (c->g.n1 % 4 || c->g.n2 % 4 || c->g.n3 % 4))
     return fail(c, CLAIRE_EINVAL, "two-level preconditioner needs every n_i %% 4 == 0");
-  if (o->hessian == 1)
-    return fail(c, CLAIRE_EINVAL, "full-Newton Hessian is not available in this build");
+  if (o->hessian == 1 && o->precision != 0)
+    return fail(c, CLAIRE_EINVAL, "full Newton needs FP32 storage (precision 0)");
+  if (o->hessian == 1 && c->mthist == nullptr) {   // full-Newton buffers on first use
+    TRY(alloc(c, &c->mthist, (int64_t)(c->nt + 1) * N_of(c)));
+    TRY(alloc(c, &c->ef, N_of(c)));
+  }
   if (o->precision == 1 && !march_supported(c->nt))
     return fail(c, CLAIRE_EINVAL, "mixed precision needs nt in {1, 2, 4, 8}");
   if (o->precision == 1 && c->mh == nullptr) {   // FP16 histories on first use
@@ -1334,6 +1435,99 @@ claire_status claire_det_deformation_gradient(claire_ctx* c, const float* v, dou
                                               float* det_out) {
   ENTER(c);
   if (!c || !v || !mmm) return CLAIRE_EINVAL;
+  return detf_stats(c, v, mmm, det_out);
+}
+
+claire_status claire_beta_search(claire_ctx* c, double eps_d, double beta0, double beta_min,
+                                 double rtol, int max_bisect, float* v_inout, double* beta_out,
+                                 double* trial_beta, double* trial_detmin, double* trial_detmax,
+                                 int max_trials, int* ntrials, claire_stats* st) {
+  ENTER(c);
+  if (!c || !v_inout || !beta_out || !(eps_d > 0.0 && eps_d < 1.0) || !(beta0 > 0.0) ||
+      !(beta_min > 0.0) || !(rtol > 0.0) || max_bisect < 0 || max_trials < 0 ||
+      (max_trials > 0 && (!trial_beta || !trial_detmin || !trial_detmax)))
+    return CLAIRE_EINVAL;
+  const int64_t N = N_of(c);
+  const size_t b3 = 3 * N * sizeof(float);
+  if (!c->vbest) TRY(alloc(c, &c->vbest, 3 * N));
+  claire_stats local{};
+  claire_stats* out = st ? st : &local;
+  memset(out, 0, sizeof *out);
+  Counters k;
+  if (ntrials) *ntrials = 0;
+  *beta_out = 0.0;
+  if (c->st != c->user) {
+    CUDA_TRY(c, cudaEventRecord(c->e1, c->user));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->e1, 0));
+  }
+  CUDA_TRY(c, cudaEventRecord(c->e0, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->v, v_inout, b3, cudaMemcpyDeviceToDevice, c->st));
+  double gnorm0 = c->opt.gnorm0;
+  int n = 0;
+  // one trial: solve at beta from the current v (the previous trial's result), then
+  // test eps_d < det F1 < 1 / eps_d (eq. ddgradbound)
+  auto trial = [&](double beta, bool* ok) -> claire_status {
+    if (beta != c->beta_v) drop_graphs(c);
+    c->beta_v = beta;
+    claire_status s = gauss_newton(c, gnorm0, k, out);
+    gnorm0 = out->gnorm0;
+    if (s != CLAIRE_OK && s != CLAIRE_ENOTCONV) return s;
+    double mmm[3] = {0.0, 0.0, 0.0};
+    TRY(detf_stats(c, c->v, mmm, nullptr));
+    *ok = eps_d < mmm[0] && mmm[1] < 1.0 / eps_d;
+    if (n < max_trials) {
+      trial_beta[n] = beta;
+      trial_detmin[n] = mmm[0];
+      trial_detmax[n] = mmm[1];
+    }
+    ++n;
+    if (*ok) CUDA_TRY(c, cudaMemcpyAsync(c->vbest, c->v, b3, cudaMemcpyDeviceToDevice, c->st));
+    return CLAIRE_OK;
+  };
+  claire_status s = CLAIRE_OK;
+  double beta = beta0, ok_beta = 0.0;
+  bool ok = false;
+  for (;;) {                                       // decades
+    s = trial(beta, &ok);
+    if (s != CLAIRE_OK || !ok) break;
+    ok_beta = beta;
+    if (beta / 10.0 < beta_min * (1.0 - 1e-9)) break;
+    beta /= 10.0;
+  }
+  if (s == CLAIRE_OK && ok_beta > 0.0 && !ok) {    // bisection (reading C-17)
+    double lo = beta, hi = ok_beta;
+    for (int i = 0; i < max_bisect && hi - lo > rtol * hi && s == CLAIRE_OK; ++i) {
+      const double mid = 0.5 * (lo + hi);
+      s = trial(mid, &ok);
+      if (s == CLAIRE_OK) (ok ? hi : lo) = mid;
+    }
+    ok_beta = hi;
+  }
+  if (ntrials) *ntrials = n;
+  if (s == CLAIRE_OK && ok_beta > 0.0) {
+    *beta_out = ok_beta;
+    if (ok_beta != c->beta_v) drop_graphs(c);
+    c->beta_v = ok_beta;
+    CUDA_TRY(c, cudaMemcpyAsync(c->v, c->vbest, b3, cudaMemcpyDeviceToDevice, c->st));
+  }
+  c->have_eval = false;
+  cudaError_t e = cudaMemcpyAsync(v_inout, c->v, b3, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess) e = cudaEventRecord(c->e1, c->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->e1);
+  if (e == cudaSuccess && c->st != c->user) e = cudaStreamWaitEvent(c->user, c->e1, 0);
+  if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "search epilogue: %s", cudaGetErrorString(e));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->e0, c->e1);
+  return finish_stats(c, out, k, ms, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+// det F1 of velocity v (Appendix, eq. def-grad): min, max and mean into mmm, the
+// field into det_out when not NULL; synchronises the stream.
+claire_status detf_stats(claire_ctx* c, const float* v, double* mmm, float* det_out) {
   const int64_t N = N_of(c);
   if (!c->detf) {
     void* p = nullptr;
@@ -1364,6 +1558,10 @@ claire_status claire_det_deformation_gradient(claire_ctx* c, const float* v, dou
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return CLAIRE_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* betas,
                                 int nlevels, float** v_inout, claire_stats* stats,

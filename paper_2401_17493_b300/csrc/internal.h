@@ -66,6 +66,12 @@ void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float
                            cudaStream_t st);
 void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st);
 void launch_div8(const Grid& g, const float* w, float* out, cudaStream_t st);
+void launch_div8_prod(const Grid& g, const float* lam, const float* w, float* out,
+                      cudaStream_t st);
+void launch_affine(int64_t n, float a, const float* x, float b, float* out, cudaStream_t st);
+void launch_ncc_final(int64_t n, const float* m1, const float* m, float* lt, const double* sx,
+                      const double* sy, double a, double b, double c, double h3,
+                      cudaStream_t st);
 void launch_sdot_hist(const Grid& g, const float* mhist, int nt, const float* vt, float scale0,
                       float* shist, cudaStream_t st);
 // With partial != NULL (nt in {1, 2, 4, 8} only, see march_supported) also

@@ -191,6 +191,41 @@ __device__ __forceinline__ float d8_axis(const float* __restrict__ u, const Grid
   return fd8(m[3], m[2], m[1], m[0], p[0], p[1], p[2], p[3], g.inv_h3);
 }
 
+// FD8 derivative along `axis` of the product lam * u at node (i1, i2, i3).
+__device__ __forceinline__ float d8_axis_prod(const float* __restrict__ lam,
+                                              const float* __restrict__ u, const Grid& g, int i1,
+                                              int i2, int i3, int axis) {
+  int64_t base, stride;
+  int i, n;
+  float ih;
+  if (axis == 0) {
+    base = (int64_t)i2 * g.n3 + i3; stride = (int64_t)g.n2 * g.n3; i = i1; n = g.n1; ih = g.inv_h1;
+  } else if (axis == 1) {
+    base = (int64_t)i1 * g.n2 * g.n3 + i3; stride = g.n3; i = i2; n = g.n2; ih = g.inv_h2;
+  } else {
+    base = ((int64_t)i1 * g.n2 + i2) * g.n3; stride = 1; i = i3; n = g.n3; ih = g.inv_h3;
+  }
+  float m[4], p[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t a = base + wrap_near(i - 1 - k, n) * stride;
+    const int64_t b = base + wrap_near(i + 1 + k, n) * stride;
+    m[k] = __ldg(lam + a) * __ldg(u + a);
+    p[k] = __ldg(lam + b) * __ldg(u + b);
+  }
+  return fd8(m[3], m[2], m[1], m[0], p[0], p[1], p[2], p[3], ih);
+}
+
+// q = div8(lam w): the full-Newton source of the incremental adjoint (eq. incadj).
+__global__ void __launch_bounds__(256) k_div8_prod(Grid g, const float* __restrict__ lam,
+                                                   const float* __restrict__ w,
+                                                   float* __restrict__ out) {
+  CLAIRE_KERNEL_INDEX
+  out[idx] = d8_axis_prod(lam, w, g, i1, i2, i3, 0) +
+             d8_axis_prod(lam, w + g.N, g, i1, i2, i3, 1) +
+             d8_axis_prod(lam, w + 2 * g.N, g, i1, i2, i3, 2);
+}
+
 __global__ void __launch_bounds__(256) k_div8(Grid g, const float* __restrict__ w,
                                               float* __restrict__ out) {
   CLAIRE_KERNEL_INDEX
@@ -468,6 +503,34 @@ __global__ void k_axpby(int64_t n, float a, const float* __restrict__ x, float b
     y[i] = fmaf(a, x[i], b * y[i]);
 }
 
+// NCC final condition of the incremental adjoint (Appendix): on entry lt = -m~(1),
+// sx = sum m1 lt and sy = sum m(1) lt (device FP64); with the L2 inner products
+// a = <m1, m(1)>, b = ||m1||^2, c = ||m(1)||^2 (h3 = cell volume):
+//   lt = (2/b)(q1 m1 + q2 m(1) - q3 m~(1)),  al = <m1, m~>, ga = <m(1), m~>,
+//   q1 = al/c - 2 a ga/c^2,  q2 = 4 a^2 ga/c^3 - 2 a al/c^2,  q3 = a^2/c^2.
+__global__ void k_ncc_final(int64_t n, const float* __restrict__ m1, const float* __restrict__ m,
+                            float* __restrict__ lt, const double* __restrict__ sx,
+                            const double* __restrict__ sy, double a, double b, double c,
+                            double h3) {
+  const double al = -h3 * *sx, ga = -h3 * *sy;
+  const float q1 = (float)(al / c - 2.0 * a * ga / (c * c));
+  const float q2 = (float)(4.0 * a * a * ga / (c * c * c) - 2.0 * a * al / (c * c));
+  const float q3 = (float)(a * a / (c * c));
+  const float f = (float)(2.0 / b);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float mt = -lt[i];
+    lt[i] = f * (fmaf(q1, m1[i], q2 * m[i]) - q3 * mt);
+  }
+}
+
+__global__ void k_affine(int64_t n, float a, const float* __restrict__ x, float b,
+                         float* __restrict__ out) {                               // out = a x + b
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = fmaf(a, x[i], b);
+}
+
 __global__ void k_lincomb(int64_t n, float a, const float* __restrict__ x, float b,
                           const float* __restrict__ y, float* __restrict__ out) {  // out = a x + b y
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -678,6 +741,21 @@ void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float
 void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st) {
   ProfileRange pr(K_GRAD8, (double)g.N * 16, st);
   k_grad8<<<grid3(g), block3(), 0, st>>>(g, u, gu);
+}
+void launch_div8_prod(const Grid& g, const float* lam, const float* w, float* out,
+                      cudaStream_t st) {
+  ProfileRange pr(K_DIV8, (double)g.N * 20, st);
+  k_div8_prod<<<grid3(g), block3(), 0, st>>>(g, lam, w, out);
+}
+void launch_ncc_final(int64_t n, const float* m1, const float* m, float* lt, const double* sx,
+                      const double* sy, double a, double b, double c, double h3,
+                      cudaStream_t st) {
+  ProfileRange pr(K_VECTOR, (double)n * 16, st);
+  k_ncc_final<<<vec_blocks(n), 256, 0, st>>>(n, m1, m, lt, sx, sy, a, b, c, h3);
+}
+void launch_affine(int64_t n, float a, const float* x, float b, float* out, cudaStream_t st) {
+  ProfileRange pr(K_VECTOR, (double)n * 8, st);
+  k_affine<<<vec_blocks(n), 256, 0, st>>>(n, a, x, b, out);
 }
 void launch_div8(const Grid& g, const float* w, float* out, cudaStream_t st) {
   ProfileRange pr(K_DIV8, (double)g.N * 16, st);

@@ -36,6 +36,8 @@ from paper_2401_17493_b300 import claire as C  # noqa: E402
 IN_CH = 16          # (m0, m1) padded to one 16-channel k-chunk
 OUT_CH = 16         # velocity in channels 0..2, padded to 16
 V_SCALE = 0.1       # network output * V_SCALE = velocity (physical units)
+PRECOND = 1         # registration solves: two-level zero-velocity preconditioner (Sec. 2.6)
+MAX_INNER = 10      # nested CG cap of that preconditioner
 
 
 def _p(t):
@@ -307,7 +309,8 @@ def solve_targets(pairs, n, beta, eps_opt=5e-2, batch=8):
         chunk = pairs[i:i + batch]
         ctxs = []
         for m0, m1 in chunk:
-            ctx = C.Context((n, n, n), nt=4, beta_v=beta, eps_opt=eps_opt, graphs=1)
+            ctx = C.Context((n, n, n), nt=4, beta_v=beta, eps_opt=eps_opt, graphs=1,
+                            precond=PRECOND, max_inner=MAX_INNER)
             ctx.set_images(m0, m1)
             ctxs.append(ctx)
         vs, stats = C.solve_batch(ctxs)
@@ -318,11 +321,15 @@ def solve_targets(pairs, n, beta, eps_opt=5e-2, batch=8):
     return out
 
 
-def train(model, inputs, targets, epochs, lr=5e-4, batch=4, seed=0, log=None):
+def train(model, inputs, targets, epochs, lr=5e-4, batch=4, seed=0, log=None, warmup=250):
+    """Adam with a linear warm-up over the first `warmup` steps, then a cosine
+    decay per epoch (the warm-up keeps the first large Adam steps from
+    silencing the ReLUs, which left the loss at the zero-prediction plateau)."""
     import torch
     rng = np.random.default_rng(seed)
     n_in = len(inputs)
     hist = []
+    step = 0
     for ep in range(epochs):
         order = rng.permutation(n_in)
         tot = 0.0
@@ -334,7 +341,8 @@ def train(model, inputs, targets, epochs, lr=5e-4, batch=4, seed=0, log=None):
             tgt = torch.cat([targets[j].reshape(3, 1, -1) for j in idx], dim=1).reshape(3, -1)
             out = model.forward(fields, len(idx))
             loss = model.loss_and_backward(out, (tgt / V_SCALE).contiguous())  # network units
-            model.step(lr_ep)
+            step += 1
+            model.step(lr_ep * min(1.0, step / max(1, warmup)))
             tot += float(loss)
             nb += 1
         hist.append(tot / max(1, nb))
@@ -355,7 +363,8 @@ def evaluate(model, pairs, n, beta, eps_opt=5e-2):
         v0 = resample(v64.contiguous(), (64, 64, 64), (n, n, n), 3).contiguous()
         torch.cuda.synchronize()
         t_pred = time.perf_counter() - t0
-        with C.Context((n, n, n), nt=4, beta_v=beta, eps_opt=eps_opt) as ctx:
+        with C.Context((n, n, n), nt=4, beta_v=beta, eps_opt=eps_opt, precond=PRECOND,
+                       max_inner=MAX_INNER) as ctx:
             ctx.set_images(m0, m1)
             z = torch.zeros((3, n, n, n), device="cuda")
             # J(0) and |g(0)| are shared by both arms (the same stopping test);
@@ -394,8 +403,11 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--beta", type=float, default=1e-2)
     ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--precond", type=int, default=PRECOND,
+                    help="registration preconditioner: 0 spectral, 1 two-level")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
+    globals()["PRECOND"] = args.precond
     from paper_2401_17493_b300 import build
     build.build()
     n = args.n

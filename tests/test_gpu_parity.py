@@ -161,6 +161,49 @@ def test_objective_gradient_and_matvec_match_oracle(claire, shape, beta_w):
     assert rel(host(Hv), OR.hessian_matvec(prob, ev, _f64(vt))) < 1e-4
 
 
+@pytest.mark.parametrize("shape", [RAGGED, (32, 32, 32)])
+def test_full_newton_matvec_matches_oracle(claire, shape):
+    """options.hessian = 1: eq. (matvec) with the lam terms (full Newton)."""
+    m0, m1, v = _pair(shape, kmax=3, disp=2.0)
+    vt = synth.bandlimited_velocity(shape, 4, 1.0, 41)
+    with claire.Context(shape, nt=4, beta_v=1e-2, hessian=1) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        ctx.objective_gradient(dev(0.5 * v))
+        Hv = ctx.hessian_matvec(dev(vt))
+        ctx.set_options(hessian=0)
+        ctx.objective_gradient(dev(0.5 * v))
+        Hgn = ctx.hessian_matvec(dev(vt))
+    prob = OR.Problem(_f64(m0), _f64(m1), 4, 1e-2)
+    ev = OR.evaluate(prob, _f64(0.5 * v))
+    ref = OR.hessian_matvec(prob, ev, _f64(vt), full_newton=True)
+    ref_gn = OR.hessian_matvec(prob, ev, _f64(vt))
+    assert rel(host(Hv), ref) < 1e-4
+    assert rel(host(Hgn), ref_gn) < 1e-4
+    assert rel(ref, ref_gn) > 1e-3                   # the extra terms are not negligible
+
+
+def test_full_newton_solve_matches_oracle(claire):
+    shape = (32, 32, 32)
+    m0, m1, _ = _pair(shape, seed=7, kmax=3, disp=1.5)
+    with claire.Context(shape, nt=4, beta_v=1e-2, max_newton=2, max_pcg=5, fixed_iters=1,
+                        hessian=1) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        v, st = ctx.solve()
+    prob = OR.Problem(_f64(m0), _f64(m1), 4, 1e-2)
+    vo, so, _ = OSV.gauss_newton(prob, None, OSV.Options(max_newton=2, max_pcg=5,
+                                                          fixed_iters=True, full_newton=True))
+    assert st.newton_iters == 2 and st.pcg_iters == so.pcg_iters
+    assert rel(host(v), vo) < 1e-3
+    assert abs(st.J - so.J) / so.J < 1e-4
+
+
+def test_full_newton_needs_fp32_storage(claire):
+    with claire.Context(RAGGED) as ctx:
+        with pytest.raises(claire.ClaireError) as e:
+            ctx.set_options(hessian=1, precision=1)
+        assert e.value.status == claire.EINVAL
+
+
 def test_matvec_before_gradient_is_an_order_error(claire):
     with claire.Context(RAGGED) as ctx:
         with pytest.raises(claire.ClaireError) as e:
