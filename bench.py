@@ -40,9 +40,11 @@ PRECOND = 1                # two-level zero-velocity preconditioner (Sec. 2.5.6,
 MAX_INNER = 10             # nested CG cap per preconditioner application
 CPU_SAMPLE_N = 32          # oracle sample: the workload restricted to 32^3
 INTERP_FD = ("trace", "sl_step", "adjoint_factor", "grad8", "div8", "sdot_hist", "accum_hist")
-# DRAM traffic per voxel and launch measured by ncu for the kernels below (see
-# profiles/); None when the kernel changed after the capture.
-NCU_TRAFFIC_PER_VOXEL = {}
+# DRAM traffic per voxel and launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) for the kernels below, from the capture summarised in
+# profiles/k_sl_256cube.md (matvec SL steps, 24 algorithmic B/voxel); drop an
+# entry when its kernel changes.
+NCU_TRAFFIC_PER_VOXEL = {"sl_step": 23.27}
 
 
 def parse():
