@@ -77,8 +77,10 @@ struct claire_ctx {
   Grid gc{};                    // coarse grid, n_i / 2 points per axis
   cufftHandle tl_r2c1 = 0, tl_c2r1 = 0, tl_r2c3 = 0, tl_c2r3 = 0;
   cufftComplex *tl_cc = nullptr, *cbuf2 = nullptr;
-  float *tl_gm = nullptr, *tl_mc = nullptr, *tl_b = nullptr, *tl_x = nullptr, *tl_r = nullptr,
-        *tl_p = nullptr, *tl_Ap = nullptr, *tl_q = nullptr;
+  // nested CG vectors as coarse half spectra [3][Ch], and two real coarse fields
+  cufftComplex *tl_sx = nullptr, *tl_sr = nullptr, *tl_sp = nullptr, *tl_sap = nullptr;
+  float *tl_gm = nullptr, *tl_mc = nullptr, *tl_q = nullptr, *tl_w = nullptr;
+  float2* tl_fw = nullptr;      // per coarse mode: R^-1/2 symbol and Parseval weight
   bool tl_ready = false, tl_image = false;
   double tl_rtol = 1e-3;        // nested CG relative tolerance of the current PCG
   int tl_iters = 0;             // nested CG iterations not yet counted in the stats
@@ -502,15 +504,22 @@ claire_status tl_setup(claire_ctx* c) {
   const int64_t Ch = (int64_t)gc.n1 * gc.n2 * (gc.n3 / 2 + 1);
   const int64_t Nh = (int64_t)g.n1 * g.n2 * (g.n3 / 2 + 1);
   // (allocations and plans made by an earlier, failed call are kept)
-  float** f3[] = {&c->tl_gm, &c->tl_b, &c->tl_x, &c->tl_r, &c->tl_p, &c->tl_Ap, &c->tl_q};
+  float** f3[] = {&c->tl_gm, &c->tl_q, &c->tl_w};
   for (auto p : f3)
     if (!*p) TRY(alloc(c, p, 3 * Nc));
   if (!c->tl_mc) TRY(alloc(c, &c->tl_mc, Nc));
-  float* p = nullptr;
-  if (!c->tl_cc) {
-    TRY(alloc(c, &p, 3 * Ch * 2));
-    c->tl_cc = (cufftComplex*)p;
+  if (!c->tl_fw) {
+    float* q = nullptr;
+    TRY(alloc(c, &q, 2 * Ch));
+    c->tl_fw = (float2*)q;
   }
+  float* p = nullptr;
+  cufftComplex** cc3[] = {&c->tl_cc, &c->tl_sx, &c->tl_sr, &c->tl_sp, &c->tl_sap};
+  for (auto q : cc3)
+    if (!*q) {
+      TRY(alloc(c, &p, 3 * Ch * 2));
+      *q = (cufftComplex*)p;
+    }
   if (!c->cbuf2) {
     TRY(alloc(c, &p, 3 * Nh * 2));
     c->cbuf2 = (cufftComplex*)p;
@@ -559,6 +568,7 @@ claire_status tl_update_image(claire_ctx* c) {
     CUFFT_TRY(c, cufftExecC2R(c->tl_c2r1, c->tl_cc, (cufftReal*)c->tl_mc));
   }
   launch_grad8(c->gc, c->tl_mc, c->tl_gm, c->st);
+  launch_tl_spec_table(c->gc, (float)c->beta_v, (float)c->gamma, c->tl_fw, c->st);
   if (c->opt.distance == 1) {
     // NCC: the pointwise part of d^2 dist / d m(1)^2 is 2 a^2 / (b c^2) times the identity
     const double w = 2.0 * c->ncc_a * c->ncc_a / (c->ncc_b * c->ncc_c * c->ncc_c);
@@ -567,23 +577,6 @@ claire_status tl_update_image(claire_ctx* c) {
   }
   TRY(check_launch(c, "two-level image"));
   c->tl_image = true;
-  return CLAIRE_OK;
-}
-
-// out = (beta_v L)^-1/2 in on the coarse grid (zero symbol set to one).
-claire_status tl_reg_inv_sqrt(claire_ctx* c, const float* in, float* out) {
-  const Grid& gc = c->gc;
-  const double bytes = 3.0 * (4.0 * gc.N + 8.0 * gc.n1 * gc.n2 * (gc.n3 / 2 + 1));
-  {
-    ProfileRange pr(K_CUFFT, bytes, c->st);
-    CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)in, c->tl_cc));
-  }
-  launch_spectral(gc, c->tl_cc, CLAIRE_OP_REG_INV_SQRT, (float)c->beta_v, (float)c->gamma, 0.f,
-                  c->st);
-  {
-    ProfileRange pr(K_CUFFT, bytes, c->st);
-    CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)out));
-  }
   return CLAIRE_OK;
 }
 
@@ -597,45 +590,47 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
   if (!c->tl_image) return fail(c, CLAIRE_EORDER, "two-level preconditioner has no image");
   const Grid& g = c->g;
   const Grid& gc = c->gc;
-  const int64_t N = g.N, n3c = 3 * gc.N;
+  const int64_t N = g.N;
   const int64_t Ch = (int64_t)gc.n1 * gc.n2 * (gc.n3 / 2 + 1);
   const double fft_f = 3.0 * (4.0 * N + 8.0 * g.n1 * g.n2 * (g.n3 / 2 + 1));
   const double fft_c = 3.0 * (4.0 * gc.N + 8.0 * Ch);
+  const float alpha = (float)c->beta_v, gamma = (float)c->gamma;
   {
     ProfileRange pr(K_CUFFT, fft_f, c->st);
     CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)r, c->cbuf));
   }
+  // right-hand side: the low modes of R^-1/2 r as a coarse spectrum (C2R normalisation)
   CUDA_TRY(c, cudaMemsetAsync(c->tl_cc, 0, 3 * Ch * sizeof(cufftComplex), c->st));
-  launch_tl_split(g, c->cbuf, c->tl_cc, 3, 1, (float)c->beta_v, (float)c->gamma,
-                  (float)(1.0 / (double)N), c->st);
-  {
-    ProfileRange pr(K_CUFFT, fft_c, c->st);
-    CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)c->tl_b));
-  }
-  // nested CG from x = 0: device scalars, one host read per iteration
-  const int nb = vector_blocks(n3c);
-  CUDA_TRY(c, cudaMemsetAsync(c->tl_x, 0, n3c * sizeof(float), c->st));
-  CUDA_TRY(c, cudaMemcpyAsync(c->tl_r, c->tl_b, n3c * sizeof(float), cudaMemcpyDeviceToDevice,
-                              c->st));
-  CUDA_TRY(c, cudaMemcpyAsync(c->tl_p, c->tl_b, n3c * sizeof(float), cudaMemcpyDeviceToDevice,
-                              c->st));
+  launch_tl_split(g, c->cbuf, c->tl_cc, 3, 1, alpha, gamma, (float)(1.0 / (double)N), c->st);
+  // nested CG on the coarse spectra: x = 0, r = p = b; device scalars, one host
+  // read per iteration; two coarse FFTs per operator application
   int cur = SLOT_TL_RR0, nxt = SLOT_TL_RR1;
-  launch_reduce(n3c, c->tl_b, nullptr, RED_SQ, c->partial, c->red_blocks, c->slots + cur, c->st);
+  launch_tl_spec_init(gc, c->tl_fw, c->tl_cc, c->tl_sx, c->tl_sr, c->tl_sp, c->partial,
+                      c->slots + cur, c->st);
   TRY(check_launch(c, "nested cg"));
   CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->slots + cur, sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   double rr = c->hres[0];
   const double stop2 = c->tl_rtol * c->tl_rtol * rr;
+  const float inv_nc = (float)(1.0 / (double)gc.N);
   int it = 0;
   while (it < c->opt.max_inner && rr > stop2 && std::isfinite(rr)) {
-    TRY(tl_reg_inv_sqrt(c, c->tl_p, c->tl_q));
-    launch_tl_outer(gc.N, c->tl_gm, c->tl_q, c->tl_Ap, c->st);
-    TRY(tl_reg_inv_sqrt(c, c->tl_Ap, c->tl_q));
-    launch_tl_finish_apply(n3c, c->tl_p, c->tl_q, c->tl_Ap, c->partial, nb,
-                           c->slots + SLOT_TL_PAP, c->st);
-    launch_tl_cg_step(n3c, c->slots + cur, c->slots + SLOT_TL_PAP, c->tl_x, c->tl_r, c->tl_p,
-                      c->tl_Ap, c->partial, nb, c->slots + nxt, c->st);
+    // A p = p + R^-1/2 (grad m_c (grad m_c . R^-1/2 p)) with R^-1/2 diagonal in k
+    launch_tl_spec_scale(gc, c->tl_fw, c->tl_sp, c->tl_cc, 1.0f, c->st);
+    {
+      ProfileRange pr(K_CUFFT, fft_c, c->st);
+      CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)c->tl_q));
+    }
+    launch_tl_outer(gc.N, c->tl_gm, c->tl_q, c->tl_w, c->st);
+    {
+      ProfileRange pr(K_CUFFT, fft_c, c->st);
+      CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)c->tl_w, c->tl_cc));
+    }
+    launch_tl_spec_finish(gc, c->tl_fw, c->tl_sp, c->tl_cc, c->tl_sap, inv_nc, c->partial,
+                          c->slots + SLOT_TL_PAP, c->st);
+    launch_tl_spec_step(gc, c->tl_fw, c->slots + cur, c->slots + SLOT_TL_PAP, c->tl_sx,
+                        c->tl_sr, c->tl_sp, c->tl_sap, c->partial, c->slots + nxt, c->st);
     TRY(check_launch(c, "nested cg"));
     CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->slots + SLOT_TL_RR0, 3 * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->st));
@@ -645,16 +640,14 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
     if (!(pAp > 0.0) || !std::isfinite(pAp)) break;   // x, r unchanged by this step
     rr = c->hres[nxt - SLOT_TL_RR0];
     if (rr <= stop2) break;
-    launch_tl_cg_dir(n3c, c->slots + nxt, c->slots + cur, c->tl_r, c->tl_p, c->st);
+    launch_tl_cg_dir(6 * Ch, c->slots + nxt, c->slots + cur, (const float*)c->tl_sr,
+                     (float*)c->tl_sp, c->st);
     std::swap(cur, nxt);
   }
   c->tl_iters += it;
-  {
-    ProfileRange pr(K_CUFFT, fft_c, c->st);
-    CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)c->tl_x, c->tl_cc));
-  }
-  launch_tl_merge(g, c->cbuf, c->tl_cc, c->cbuf2, (float)c->beta_v, (float)c->gamma,
-                  (float)(1.0 / (double)N), (float)(1.0 / (double)gc.N), c->st);
+  // prolong the coarse solution (already a spectrum), keep the high modes, R^-1/2
+  launch_tl_merge(g, c->cbuf, c->tl_sx, c->cbuf2, alpha, gamma, (float)(1.0 / (double)N), 1.0f,
+                  c->st);
   {
     ProfileRange pr(K_CUFFT, 2 * fft_f, c->st);
     CUFFT_TRY(c, cufftExecC2R(c->c2r, c->cbuf, (cufftReal*)z));

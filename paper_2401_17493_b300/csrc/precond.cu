@@ -1,7 +1,8 @@
 // Two-level zero-velocity preconditioner (Sec. 2.5.6): the spectral kernels
 // that split a residual into the part restricted to the grid of half the
 // resolution and the high-frequency remainder, merge the coarse solution back,
-// and the pointwise and vector kernels of the nested CG on the coarse grid.
+// and the kernels of the nested CG, which runs on coarse spectra (the
+// pointwise outer product is the only real-space step).
 //
 // Fine half spectra are [3][n1][n2][n3/2+1] (cuFFT R2C layout), coarse ones
 // [3][n1/2][n2/2][n3/4+1].  A fine mode is "low" when |k_i| < n_i / 4 on every
@@ -111,44 +112,6 @@ __global__ void k_tl_outer(int64_t n, const float* __restrict__ gm, const float*
   }
 }
 
-// Ap = p + y and this block's share of <p, Ap>.
-__global__ void __launch_bounds__(256) k_tl_finish_apply(int64_t n, const float* __restrict__ p,
-                                                         const float* __restrict__ y,
-                                                         float* __restrict__ Ap,
-                                                         double* __restrict__ partial) {
-  KahanF acc;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float a = p[i] + y[i];
-    Ap[i] = a;
-    acc.add(p[i] * a);
-  }
-  const double b = block_sum(acc.value());
-  if (threadIdx.x == 0) partial[blockIdx.x] = b;
-}
-
-// CG step: a = rr / pAp (0 when pAp <= 0 or not finite), x += a p, r -= a Ap,
-// and this block's share of ||r||^2.
-__global__ void __launch_bounds__(256) k_tl_cg_step(int64_t n, const double* __restrict__ rr,
-                                                    const double* __restrict__ pAp,
-                                                    float* __restrict__ x, float* __restrict__ r,
-                                                    const float* __restrict__ p,
-                                                    const float* __restrict__ Ap,
-                                                    double* __restrict__ partial) {
-  const double q = *pAp;
-  const float a = (q > 0.0 && isfinite(q)) ? (float)(*rr / q) : 0.0f;
-  KahanF acc;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fmaf(a, p[i], x[i]);
-    const float rv = fmaf(-a, Ap[i], r[i]);
-    r[i] = rv;
-    acc.add(rv * rv);
-  }
-  const double b = block_sum(acc.value());
-  if (threadIdx.x == 0) partial[blockIdx.x] = b;
-}
-
 // p = r + (rr_new / rr_old) p.
 __global__ void k_tl_cg_dir(int64_t n, const double* __restrict__ rr_new,
                             const double* __restrict__ rr_old, const float* __restrict__ r,
@@ -158,6 +121,136 @@ __global__ void k_tl_cg_dir(int64_t n, const double* __restrict__ rr_new,
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fmaf(b, p[i], r[i]);
 }
+
+// ---- nested CG in the coarse spectral domain.  Vectors are coarse half spectra
+// [3][Ch] in the normalisation of cuFFT's unnormalised C2R (u = C2R(u^)), so the
+// split kernel's output is the right-hand side and the merge kernel reads the
+// solution directly.  Inner products are Parseval sums over the half spectrum:
+// modes with k3 = 0 or k3 = n3/2 count once, the others twice (the common factor
+// N_c drops out of every CG ratio).
+
+// Per coarse mode: x = R^-1/2 symbol, y = Parseval weight (1 for k3 = 0 or
+// k3 = n3/2, else 2).  Rebuilt whenever beta_v may have changed.
+__global__ void k_tl_spec_table(int64_t Ch, int n1, int n2, int n3, float alpha, float gamma,
+                                float2* __restrict__ fw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ch) return;
+  const int nh = n3 / 2 + 1;
+  const int j3 = (int)(i % nh);
+  const int j2 = (int)((i / nh) % n2);
+  const int j1 = (int)(i / ((int64_t)nh * n2));
+  const int k1 = j1 <= n1 / 2 ? j1 : j1 - n1;
+  const int k2 = j2 <= n2 / 2 ? j2 : j2 - n2;
+  fw[i] = make_float2(inv_sqrt_symbol(k1, k2, j3, alpha, gamma),
+                      (j3 == 0 || 2 * j3 == n3) ? 1.0f : 2.0f);
+}
+
+// The kernels below run a grid-stride loop over the Ch modes; each thread
+// handles the three fields of a mode (one table read), and the partial sums go
+// to partial[blockIdx.x].
+#define CLAIRE_SPEC_LOOP                                                                  \
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < Ch;                \
+       m += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ void spec_partial(double* partial, const KahanF& acc) {
+  const double b = block_sum(acc.value());
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
+// out = scale R^-1/2 in.
+__global__ void k_tl_spec_scale(int64_t Ch, const float2* __restrict__ fw,
+                                const cufftComplex* __restrict__ in,
+                                cufftComplex* __restrict__ out, float scale) {
+  CLAIRE_SPEC_LOOP {
+    const float f = scale * fw[m].x;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cufftComplex v = in[a * Ch + m];
+      out[a * Ch + m] = make_cuComplex(f * v.x, f * v.y);
+    }
+  }
+}
+
+// Ap = p + scale R^-1/2 y (y = R2C of the pointwise product) and the block's
+// share of <p, Ap>.
+__global__ void __launch_bounds__(256) k_tl_spec_finish(int64_t Ch, const float2* __restrict__ fw,
+                                                        const cufftComplex* __restrict__ p,
+                                                        const cufftComplex* __restrict__ y,
+                                                        cufftComplex* __restrict__ Ap,
+                                                        float scale,
+                                                        double* __restrict__ partial) {
+  KahanF acc;
+  CLAIRE_SPEC_LOOP {
+    const float2 t = fw[m];
+    const float f = scale * t.x;
+    float d = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cufftComplex pv = p[c * Ch + m], yv = y[c * Ch + m];
+      const cufftComplex a = make_cuComplex(fmaf(f, yv.x, pv.x), fmaf(f, yv.y, pv.y));
+      Ap[c * Ch + m] = a;
+      d = fmaf(pv.x, a.x, fmaf(pv.y, a.y, d));
+    }
+    acc.add(t.y * d);
+  }
+  spec_partial(partial, acc);
+}
+
+// CG step on spectra: a = rr / pAp (0 when pAp <= 0 or not finite), x += a p,
+// r -= a Ap, and the block's share of ||r||^2.
+__global__ void __launch_bounds__(256) k_tl_spec_step(int64_t Ch, const float2* __restrict__ fw,
+                                                      const double* __restrict__ rr,
+                                                      const double* __restrict__ pAp,
+                                                      cufftComplex* __restrict__ x,
+                                                      cufftComplex* __restrict__ r,
+                                                      const cufftComplex* __restrict__ p,
+                                                      const cufftComplex* __restrict__ Ap,
+                                                      double* __restrict__ partial) {
+  const double q = *pAp;
+  const float a = (q > 0.0 && isfinite(q)) ? (float)(*rr / q) : 0.0f;
+  KahanF acc;
+  CLAIRE_SPEC_LOOP {
+    float d = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t i = c * Ch + m;
+      const cufftComplex pv = p[i], av = Ap[i];
+      cufftComplex xv = x[i], rv = r[i];
+      xv.x = fmaf(a, pv.x, xv.x); xv.y = fmaf(a, pv.y, xv.y);
+      rv.x = fmaf(-a, av.x, rv.x); rv.y = fmaf(-a, av.y, rv.y);
+      x[i] = xv;
+      r[i] = rv;
+      d = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, d));
+    }
+    acc.add(fw[m].y * d);
+  }
+  spec_partial(partial, acc);
+}
+
+// x = 0, r = p = b, and the block's share of ||b||^2.
+__global__ void __launch_bounds__(256) k_tl_spec_init(int64_t Ch, const float2* __restrict__ fw,
+                                                      const cufftComplex* __restrict__ b,
+                                                      cufftComplex* __restrict__ x,
+                                                      cufftComplex* __restrict__ r,
+                                                      cufftComplex* __restrict__ p,
+                                                      double* __restrict__ partial) {
+  KahanF acc;
+  CLAIRE_SPEC_LOOP {
+    float d = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t i = c * Ch + m;
+      const cufftComplex v = b[i];
+      x[i] = make_cuComplex(0.f, 0.f);
+      r[i] = v;
+      p[i] = v;
+      d = fmaf(v.x, v.x, fmaf(v.y, v.y, d));
+    }
+    acc.add(fw[m].y * d);
+  }
+  spec_partial(partial, acc);
+}
+#undef CLAIRE_SPEC_LOOP
 
 // FP16 field (scaled by sig) -> FP32 field / sig.
 __global__ void k_tl_unscale_h(int64_t n, const __half* __restrict__ h, float inv,
@@ -190,29 +283,61 @@ void launch_tl_outer(int64_t n, const float* gm, const float* q, float* w, cudaS
   k_tl_outer<<<vector_blocks(n), 256, 0, st>>>(n, gm, q, w);
 }
 
-void launch_tl_finish_apply(int64_t n, const float* p, const float* y, float* Ap,
-                            double* partial, int nblocks, double* pAp, cudaStream_t st) {
-  {
-    ProfileRange pr(K_PRECOND, (double)n * 12, st);
-    k_tl_finish_apply<<<nblocks, 256, 0, st>>>(n, p, y, Ap, partial);
-  }
-  launch_reduce_final(partial, nblocks, RED_SUM, pAp, st);
-}
-
-void launch_tl_cg_step(int64_t n, const double* rr, const double* pAp, float* x, float* r,
-                       const float* p, const float* Ap, double* partial, int nblocks,
-                       double* rr_new, cudaStream_t st) {
-  {
-    ProfileRange pr(K_PRECOND, (double)n * 24, st);
-    k_tl_cg_step<<<nblocks, 256, 0, st>>>(n, rr, pAp, x, r, p, Ap, partial);
-  }
-  launch_reduce_final(partial, nblocks, RED_SUM, rr_new, st);
-}
-
 void launch_tl_cg_dir(int64_t n, const double* rr_new, const double* rr_old, const float* r,
                       float* p, cudaStream_t st) {
   ProfileRange pr(K_PRECOND, (double)n * 12, st);
   k_tl_cg_dir<<<vector_blocks(n), 256, 0, st>>>(n, rr_new, rr_old, r, p);
+}
+
+static int64_t coarse_half(const Grid& gc) { return (int64_t)gc.n1 * gc.n2 * (gc.n3 / 2 + 1); }
+static unsigned spec_grid(const Grid& gc) { return (unsigned)vector_blocks(coarse_half(gc)); }
+int tl_spec_blocks(const Grid& gc) { return vector_blocks(coarse_half(gc)); }
+
+void launch_tl_spec_table(const Grid& gc, float alpha, float gamma, float2* fw, cudaStream_t st) {
+  const int64_t Ch = coarse_half(gc);
+  ProfileRange pr(K_PRECOND, (double)Ch * 8, st);
+  k_tl_spec_table<<<nblk(Ch), 256, 0, st>>>(Ch, gc.n1, gc.n2, gc.n3, alpha, gamma, fw);
+}
+
+void launch_tl_spec_scale(const Grid& gc, const float2* fw, const cufftComplex* in,
+                          cufftComplex* out, float scale, cudaStream_t st) {
+  const int64_t Ch = coarse_half(gc);
+  ProfileRange pr(K_PRECOND, (double)Ch * 3 * 16, st);
+  k_tl_spec_scale<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, in, out, scale);
+}
+
+void launch_tl_spec_finish(const Grid& gc, const float2* fw, const cufftComplex* p,
+                           const cufftComplex* y, cufftComplex* Ap, float scale, double* partial,
+                           double* pAp, cudaStream_t st) {
+  const int64_t Ch = coarse_half(gc);
+  {
+    ProfileRange pr(K_PRECOND, (double)Ch * 3 * 24, st);
+    k_tl_spec_finish<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, p, y, Ap, scale, partial);
+  }
+  launch_reduce_final(partial, tl_spec_blocks(gc), RED_SUM, pAp, st);
+}
+
+void launch_tl_spec_step(const Grid& gc, const float2* fw, const double* rr, const double* pAp,
+                         cufftComplex* x, cufftComplex* r, const cufftComplex* p,
+                         const cufftComplex* Ap, double* partial, double* rr_new,
+                         cudaStream_t st) {
+  const int64_t Ch = coarse_half(gc);
+  {
+    ProfileRange pr(K_PRECOND, (double)Ch * 3 * 48, st);
+    k_tl_spec_step<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, rr, pAp, x, r, p, Ap, partial);
+  }
+  launch_reduce_final(partial, tl_spec_blocks(gc), RED_SUM, rr_new, st);
+}
+
+void launch_tl_spec_init(const Grid& gc, const float2* fw, const cufftComplex* b, cufftComplex* x,
+                         cufftComplex* r, cufftComplex* p, double* partial, double* bb,
+                         cudaStream_t st) {
+  const int64_t Ch = coarse_half(gc);
+  {
+    ProfileRange pr(K_PRECOND, (double)Ch * 3 * 32, st);
+    k_tl_spec_init<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, b, x, r, p, partial);
+  }
+  launch_reduce_final(partial, tl_spec_blocks(gc), RED_SUM, bb, st);
 }
 
 void launch_tl_unscale_h(int64_t n, const __half* h, float inv, float* out, cudaStream_t st) {
