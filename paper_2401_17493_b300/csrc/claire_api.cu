@@ -57,6 +57,7 @@ struct claire_ctx {
   // det F workspace (allocated on first use)
   float* detf = nullptr;
   bool have_eval = false;
+  bool lv_spectrum = false;     // cbuf holds the spectrum of L v of the last objective()
   double J = 0.0, dist = 0.0;
   // NCC distance (options.distance = 1): <m1, m(1)>, ||m1||^2, ||m(1)||^2 (L2, with h^3)
   // of the last objective evaluation
@@ -192,6 +193,7 @@ claire_status spectral(claire_ctx* c, int op, const float* in, float* out, doubl
   const double fft_bytes = 3.0 * (4.0 * c->g.N + 8.0 * c->g.n1 * c->g.n2 * (c->g.n3 / 2 + 1));
   {
     ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    c->lv_spectrum = false;
     CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)in, c->cbuf));
   }
   launch_spectral(c->g, c->cbuf, op, (float)alpha, (float)c->gamma, (float)c->opt.beta_w, c->st);
@@ -304,8 +306,22 @@ claire_status objective(claire_ctx* c, const float* v, double* J) {
   } else {
     TRY(reduce(c, N, c->mhist + c->nt * N, c->m1, RED_SQDIFF, &sq));
   }
-  TRY(spectral(c, CLAIRE_OP_L, v, c->Lv, 1.0));
-  TRY(dot3(c, v, c->Lv, &vLv));
+  // <v, L v> by Parseval from the spectrum of v; L v itself is only formed for the
+  // point whose gradient is taken (lv_spectrum: cbuf holds L v^ until then)
+  {
+    const Grid& g = c->g;
+    const double fft_bytes = 3.0 * (4.0 * g.N + 8.0 * g.n1 * g.n2 * (g.n3 / 2 + 1));
+    ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)v, c->cbuf));
+  }
+  launch_spectral(c->g, c->cbuf, CLAIRE_OP_L, 1.0f, (float)c->gamma, (float)c->opt.beta_w, c->st,
+                  c->partial);
+  launch_reduce_final(c->partial, spectral_blocks(c->g), RED_SUM, c->dres, c->st);
+  TRY(check_launch(c, "objective"));
+  CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  vLv = c->hres[0];
+  c->lv_spectrum = true;
   c->dist = c->opt.distance == 1 ? 1.0 - c->ncc_a * c->ncc_a / (c->ncc_b * c->ncc_c)
                                   : 0.5 * h3 * sq;
   *J = c->dist + 0.5 * c->beta_v * h3 * vLv;
@@ -318,6 +334,14 @@ claire_status objective(claire_ctx* c, const float* v, double* J) {
 claire_status adjoint_and_gradient(claire_ctx* c) {
   const int64_t N = N_of(c);
   const Grid& g = c->g;
+  if (c->lv_spectrum) {                            // L v of the point objective() evaluated
+    const double fft_bytes = 3.0 * (4.0 * g.N + 8.0 * g.n1 * g.n2 * (g.n3 / 2 + 1));
+    ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    CUFFT_TRY(c, cufftExecC2R(c->c2r, c->cbuf, (cufftReal*)c->Lv));
+    c->lv_spectrum = false;
+  } else {
+    TRY(spectral(c, CLAIRE_OP_L, c->v, c->Lv, 1.0));
+  }
   launch_trace(g, c->v, nullptr, c->db, ht_of(c), c->st);
   launch_div8(g, c->v, c->D, c->st);
   launch_adjoint_factor(g, c->D, c->db, ht_of(c), c->cf, c->st);
@@ -558,6 +582,7 @@ claire_status tl_update_image(claire_ctx* c) {
   const double bytes = 4.0 * N + 8.0 * g.n1 * g.n2 * (g.n3 / 2 + 1);
   {
     ProfileRange pr(K_CUFFT, bytes, c->st);
+    c->lv_spectrum = false;
     CUFFT_TRY(c, cufftExecR2C(c->tl_r2c1, (cufftReal*)m1p, c->cbuf));
   }
   const int64_t Ch = (int64_t)c->gc.n1 * c->gc.n2 * (c->gc.n3 / 2 + 1);
@@ -597,6 +622,7 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
   const float alpha = (float)c->beta_v, gamma = (float)c->gamma;
   {
     ProfileRange pr(K_CUFFT, fft_f, c->st);
+    c->lv_spectrum = false;
     CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)r, c->cbuf));
   }
   // right-hand side: the low modes of R^-1/2 r as a coarse spectrum (C2R normalisation)
@@ -667,6 +693,7 @@ claire_status precondition(claire_ctx* c, int rz_slot) {
   const double fft_bytes = 3.0 * (4.0 * c->g.N + 8.0 * c->g.n1 * c->g.n2 * (c->g.n3 / 2 + 1));
   {
     ProfileRange pr(K_CUFFT, fft_bytes, c->st);
+    c->lv_spectrum = false;
     CUFFT_TRY(c, cufftExecR2C(c->r2c, (cufftReal*)c->r, c->cbuf));
   }
   launch_spectral(c->g, c->cbuf, CLAIRE_OP_REG_INV, (float)c->beta_v, (float)c->gamma,
