@@ -58,6 +58,8 @@ struct claire_ctx {
   float* detf = nullptr;
   bool have_eval = false;
   bool lv_spectrum = false;     // cbuf holds the spectrum of L v of the last objective()
+  double vLv = 0.0;             // <v, L v> (plain sum) of the last objective()
+  double beta_eval = 0.0;       // beta_v of the stored J and g
   double J = 0.0, dist = 0.0;
   // NCC distance (options.distance = 1): <m1, m(1)>, ||m1||^2, ||m(1)||^2 (L2, with h^3)
   // of the last objective evaluation
@@ -321,6 +323,7 @@ claire_status objective(claire_ctx* c, const float* v, double* J) {
   CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   vLv = c->hres[0];
+  c->vLv = vLv;
   c->lv_spectrum = true;
   c->dist = c->opt.distance == 1 ? 1.0 - c->ncc_a * c->ncc_a / (c->ncc_b * c->ncc_c)
                                   : 0.5 * h3 * sq;
@@ -375,7 +378,20 @@ claire_status adjoint_and_gradient(claire_ctx* c) {
     TRY(accumulate(c, c->lhist, c->lh, c->Lv, (float)c->beta_v, c->grad, nullptr, nullptr,
                    nullptr));
   }
+  c->beta_eval = c->beta_v;
   return check_launch(c, "gradient");
+}
+
+// The stored evaluation at a new beta_v (continuation, Sec. 2.6): the state, the
+// adjoint and the data term b do not depend on beta_v (beta_w = 0), so
+// g = beta_v L v + b and J = dist + beta_v/2 h^3 <v, L v> change by the
+// regulariser alone.
+claire_status rebeta(claire_ctx* c) {
+  const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
+  launch_axpby(3 * N_of(c), (float)(c->beta_v - c->beta_eval), c->Lv, 1.0f, c->grad, c->st);
+  c->J = c->dist + 0.5 * c->beta_v * h3 * c->vLv;
+  c->beta_eval = c->beta_v;
+  return check_launch(c, "rebeta");
 }
 
 // Full evaluation at c->v: trace, state, J, adjoint, g (Algorithm 1, lines 3-6).
@@ -969,9 +985,15 @@ claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_sta
     k.pde += 2;
     TRY(absmax3(c, c->grad, &gnorm0));
     std::swap(c->v, c->vtrial);
+    c->have_eval = false;                          // the evaluation belongs to v = 0
   }
-  TRY(evaluate(c));
-  k.pde += 2;
+  if (c->have_eval && c->opt.beta_w <= 0.0) {
+    // continuation: the previous level ended evaluated at this v
+    if (c->beta_eval != c->beta_v) TRY(rebeta(c));
+  } else {
+    TRY(evaluate(c));
+    k.pde += 2;
+  }
   if (c->opt.autotune && !c->tuned) TRY(autotune(c));
   double gn = 0.0;
   TRY(absmax3(c, c->grad, &gn));
@@ -1332,6 +1354,7 @@ static claire_status solve_levels(claire_ctx* c, const double* betas, int nlev, 
   }
   CUDA_TRY(c, cudaEventRecord(c->e0, c->st));
   if (v_in) CUDA_TRY(c, cudaMemcpyAsync(c->v, v_in, b3, cudaMemcpyDeviceToDevice, c->st));
+  c->have_eval = false;                            // evaluated afresh at the initial guess
   double gnorm0 = c->opt.gnorm0;
   claire_status s = CLAIRE_OK;
   for (int i = 0; i < nlev; ++i) {
@@ -1482,6 +1505,7 @@ claire_status claire_beta_search(claire_ctx* c, double eps_d, double beta0, doub
   }
   CUDA_TRY(c, cudaEventRecord(c->e0, c->st));
   CUDA_TRY(c, cudaMemcpyAsync(c->v, v_inout, b3, cudaMemcpyDeviceToDevice, c->st));
+  c->have_eval = false;
   double gnorm0 = c->opt.gnorm0;
   int n = 0;
   // one trial: solve at beta from the current v (the previous trial's result), then
