@@ -265,9 +265,21 @@ claire_status accumulate_newton(claire_ctx* c, float* out, const float* dotv, do
   return check_launch(c, "full-Newton accumulate");
 }
 
+// The FP32 state, adjoint and incremental histories ((n_t + 1) N floats each),
+// allocated on first FP32 use: the mixed-precision form never needs them.
+claire_status fp32_histories(claire_ctx* c) {
+  if (c->mhist && c->lhist && c->shist && c->lthist) return CLAIRE_OK;
+  const int64_t nh = (int64_t)(c->nt + 1) * N_of(c);
+  float** hists[] = {&c->mhist, &c->lhist, &c->shist, &c->lthist};
+  for (auto p : hists)
+    if (!*p) TRY(alloc(c, p, nh));
+  return CLAIRE_OK;
+}
+
 // m^0 = m0, m^{j+1}(x) = m^j(x + d_f(x))  (eq. transport, homogeneous SL steps)
 claire_status state_solve(claire_ctx* c, const float* d) {
   const int64_t N = N_of(c);
+  if (!mixed(c)) TRY(fp32_histories(c));
   if (mixed(c)) {                                  // FP16 history of sig_m m
     launch_axpy_h(N, c->sig_m, c->m0, 0.0f, nullptr, c->mh, c->st);
     for (int j = 0; j < c->nt; ++j)
@@ -1158,8 +1170,6 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
   for (auto p : fields1) if (s == CLAIRE_OK) s = alloc(c, p, N);
   for (auto p : fields3) if (s == CLAIRE_OK) s = alloc(c, p, 3 * N);
   c->dbuf0 = c->df;
-  float** hists[] = {&c->mhist, &c->lhist, &c->shist, &c->lthist};
-  for (auto p : hists) if (s == CLAIRE_OK) s = alloc(c, p, (int64_t)(nt + 1) * N);
   const int64_t Nc = (int64_t)nx * ny * (nz / 2 + 1);
   if (s == CLAIRE_OK) {
     float* cb = nullptr;
@@ -1232,6 +1242,7 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
     return fail(c, CLAIRE_EINVAL, "two-level preconditioner needs every n_i %% 4 == 0");
   if (o->hessian == 1 && o->precision != 0)
     return fail(c, CLAIRE_EINVAL, "full Newton needs FP32 storage (precision 0)");
+  if (o->precision == 0) TRY(fp32_histories(c));
   if (o->hessian == 1 && c->mthist == nullptr) {   // full-Newton buffers on first use
     TRY(alloc(c, &c->mthist, (int64_t)(c->nt + 1) * N_of(c)));
     TRY(alloc(c, &c->ef, N_of(c)));

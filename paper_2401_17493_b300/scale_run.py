@@ -28,6 +28,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--beta", type=float, default=1e-3)
     ap.add_argument("--matvecs", type=int, default=10)
+    ap.add_argument("--precond", type=int, default=1, help="0 spectral, 1 two-level")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     build.build()
@@ -38,7 +39,7 @@ def main():
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     ctx = claire.Context(shape, nt=4, beta_v=args.beta, precision=args.precision, eps_opt=5e-2,
-                         max_pcg=200)
+                         max_pcg=200, precond=args.precond, max_inner=10)
     ctx.set_images(m0, m1)
     del m0, m1
     torch.cuda.empty_cache()
@@ -70,8 +71,10 @@ def main():
     sl = kern.get("sl_step", {})
     res = {
         "grid": shape, "voxels": n ** 3, "precision": "fp16 fields" if args.precision else "fp32",
+        "precond": "two-level" if args.precond else "spectral",
         "beta_v": args.beta, "generate_s": t_gen, "solve_s": t_solve,
-        "newton_iters": st.newton_iters, "matvecs": st.matvecs, "grad_rel": st.grad_rel,
+        "newton_iters": st.newton_iters, "matvecs": st.matvecs, "inner_iters": st.inner_iters,
+        "grad_rel": st.grad_rel,
         "mismatch_rel": st.mismatch_rel, "status": st.status,
         "matvecs_per_s": mv_s,
         "workspace_gb": ctx.workspace_bytes / 1e9,
