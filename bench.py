@@ -50,7 +50,7 @@ NCU_TRAFFIC_PER_VOXEL = {"sl_step": 23.27}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="claire", choices=["claire", "reference"])
     ap.add_argument("--size", type=int, default=256)
