@@ -64,6 +64,23 @@ def test_mixed_objective_gradient_and_matvec_errors(claire, shape):
     assert eJ < 2e-3 and eg < 2e-2 and eH < 2e-2
 
 
+@pytest.mark.parametrize("nt", [2, 8])
+def test_mixed_other_time_step_counts(claire, nt):
+    shape = (24, 20, 16)
+    m0, m1, vtrue = synth.blob_pair(shape, seed=2, kmax=3, max_disp_voxels=2.0)
+    v = 0.4 * vtrue
+    vt = synth.bandlimited_velocity(shape, 4, 1.5, 29).astype(np.float32)
+    prob = OR.Problem(f64(m0), f64(m1), nt, 1e-2)
+    ev = OR.evaluate(prob, f64(v))
+    with claire.Context(shape, nt=nt, beta_v=1e-2, precision=1) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        J, g = ctx.objective_gradient(dev(v))
+        Hv = ctx.hessian_matvec(dev(vt))
+    assert abs(J - ev.J) / ev.J < 2e-3
+    assert rel(host(g), ev.g) < 2e-2
+    assert rel(host(Hv), OR.hessian_matvec(prob, ev, f64(vt))) < 2e-2
+
+
 def test_mixed_images_far_from_unit_range_are_scaled(claire):
     shape = RAGGED
     m0, m1, vtrue = synth.blob_pair(shape, seed=2)

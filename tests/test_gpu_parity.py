@@ -161,6 +161,25 @@ def test_objective_gradient_and_matvec_match_oracle(claire, shape, beta_w):
     assert rel(host(Hv), OR.hessian_matvec(prob, ev, _f64(vt))) < 1e-4
 
 
+@pytest.mark.parametrize("nt", [1, 2, 3, 8])
+def test_other_time_step_counts_match_oracle(claire, nt):
+    """n_t in {1, 2, 8} uses the FD8 march with 2, 3, 9 history fields; n_t = 3 the
+    per-node fallback kernels."""
+    shape = (24, 20, 16)
+    m0, m1, vtrue = _pair(shape, kmax=3, disp=2.0)
+    v = 0.4 * vtrue
+    vt = synth.bandlimited_velocity(shape, 4, 1.5, 19).astype(np.float32)
+    with claire.Context(shape, nt=nt, beta_v=1e-2) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        J, g = ctx.objective_gradient(dev(v))
+        Hv = ctx.hessian_matvec(dev(vt))
+    prob = OR.Problem(_f64(m0), _f64(m1), nt, 1e-2)
+    ev = OR.evaluate(prob, _f64(v))
+    assert abs(J - ev.J) / abs(ev.J) < 1e-5
+    assert rel(host(g), ev.g) < 1e-4
+    assert rel(host(Hv), OR.hessian_matvec(prob, ev, _f64(vt))) < 1e-4
+
+
 @pytest.mark.parametrize("shape", [RAGGED, (32, 32, 32)])
 def test_full_newton_matvec_matches_oracle(claire, shape):
     """options.hessian = 1: eq. (matvec) with the lam terms (full Newton)."""
