@@ -67,11 +67,13 @@ typedef struct {
                            solve and keep the fastest for this context (default 0)   */
   int graphs;           /* 1: replay each PCG iteration as a captured CUDA graph      */
   int precond;          /* PCG preconditioner (Sec. 2.5.6).  0: spectral, (beta_v L)^-1
-                           with the zero symbol set to one (default).  1: two-level
+                           with the zero symbol set to one.  1: two-level
                            zero-velocity H0: R^-1/2 M^-1 R^-1/2 with R = beta_v L, M^-1
                            the coarse (n/2) solve of I + R^-1/2 (grad m (x) grad m)
                            R^-1/2 at the current m(1) plus the high-frequency part;
-                           needs every n_i % 4 == 0                                  */
+                           needs every n_i % 4 == 0 (EINVAL otherwise).  2 (default):
+                           two-level when every n_i % 4 == 0, else spectral -- the
+                           paper's default preconditioner where it applies (Sec. 2.6) */
   int max_inner;        /* nested CG iteration cap of precond 1 (default 50)          */
   double inner_rtol;    /* > 0: fixed relative tolerance of the nested CG; <= 0: one
                            tenth of the outer PCG's relative tolerance (Sec. 2.6)    */

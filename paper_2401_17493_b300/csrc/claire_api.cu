@@ -219,6 +219,11 @@ claire_status project_data_term(claire_ctx* c, float* b) {
 
 float ht_of(const claire_ctx* c) { return 1.0f / (float)c->nt; }
 bool mixed(const claire_ctx* c) { return c->opt.precision == 1; }
+bool grid_div4(const claire_ctx* c) { return c->g.n1 % 4 == 0 && c->g.n2 % 4 == 0 && c->g.n3 % 4 == 0; }
+// options.precond 1, or 2 (automatic) on a grid whose sizes are multiples of 4
+bool two_level(const claire_ctx* c) {
+  return c->opt.precond == 1 || (c->opt.precond == 2 && grid_div4(c));
+}
 
 // Slots of the device-side FP64 scalars.
 enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4, SLOT_VMAX = 8,
@@ -717,7 +722,7 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
 // With options.precond = 1 the two-level preconditioner instead, with
 // beta_v L z in scr3.
 claire_status precondition(claire_ctx* c, int rz_slot) {
-  if (c->opt.precond == 1) return tl_precondition(c, c->r, c->z, c->scr3, rz_slot);
+  if (two_level(c)) return tl_precondition(c, c->r, c->z, c->scr3, rz_slot);
   const double fft_bytes = 3.0 * (4.0 * c->g.N + 8.0 * c->g.n1 * c->g.n2 * (c->g.n3 / 2 + 1));
   {
     ProfileRange pr(K_CUFFT, fft_bytes, c->st);
@@ -779,9 +784,9 @@ claire_status pcg_part_a(claire_ctx* c, int cur) {
 
 // beta_v L z for the recurrence of beta_v L s: r - mean(r) for the spectral
 // preconditioner, the field computed with z for the two-level one.
-const float* lz_source(const claire_ctx* c) { return c->opt.precond == 1 ? c->scr3 : c->r; }
+const float* lz_source(const claire_ctx* c) { return two_level(c) ? c->scr3 : c->r; }
 const double* lz_means(const claire_ctx* c) {
-  return c->slots + (c->opt.precond == 1 ? SLOT_ZERO : SLOT_MEAN);
+  return c->slots + (two_level(c) ? SLOT_ZERO : SLOT_MEAN);
 }
 
 claire_status pcg_part_b(claire_ctx* c, int cur, int nxt) {
@@ -809,7 +814,7 @@ void drop_graphs(claire_ctx* c) {
 claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
   // the nested CG of the two-level preconditioner reads its residual on the
   // host, so part B is not captured then
-  if (!c->opt.graphs || (which == 1 && c->opt.precond == 1))
+  if (!c->opt.graphs || (which == 1 && two_level(c)))
     return which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
   const int slot = 4 * (c->df == c->dbuf0 ? 0 : 1) + 2 * which + (cur == SLOT_RZ0 ? 0 : 1);
   if (!c->graph_exec[slot]) {
@@ -1022,7 +1027,7 @@ claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_sta
     double gg = 0.0;
     TRY(dot3(c, c->grad, c->grad, &gg));
     claire_status curv = CLAIRE_OK;
-    if (c->opt.precond == 1) {
+    if (two_level(c)) {
       // H0 at the current m(1); nested tolerance a tenth of the outer one (Sec. 2.6)
       TRY(tl_update_image(c));
       c->tl_rtol = c->opt.inner_rtol > 0.0 ? c->opt.inner_rtol : 0.1 * eta;
@@ -1113,7 +1118,7 @@ claire_status claire_default_options(claire_options* o) {
   o->forcing = 0;
   o->stream = nullptr;
   o->verbose = 0;
-  o->precond = 0;
+  o->precond = 2;
   o->max_inner = 50;
   o->inner_rtol = 0.0;
   o->distance = 0;
@@ -1232,8 +1237,8 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
   if (!c || !o) return CLAIRE_EINVAL;
   if (o->precision < 0 || o->precision > 1 || o->hessian < 0 || o->hessian > 1 ||
       !(o->beta_w >= 0.0) || !(o->eps_opt > 0.0) || o->max_newton < 0 || o->max_pcg < 1 ||
-      o->forcing < 0 || o->forcing > 1 || o->precond < 0 || o->precond > 1 ||
-      (o->precond == 1 && o->max_inner < 1) || !std::isfinite(o->inner_rtol) ||
+      o->forcing < 0 || o->forcing > 1 || o->precond < 0 || o->precond > 2 ||
+      (o->precond != 0 && o->max_inner < 1) || !std::isfinite(o->inner_rtol) ||
       o->distance < 0 || o->distance > 1)
     return fail(c, CLAIRE_EINVAL, "invalid option value");
   if (o->distance == 1 && o->precision != 0)
@@ -1272,7 +1277,7 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
   c->st = o->graphs ? c->own : c->user;
   CUFFT_TRY(c, cufftSetStream(c->r2c, c->st));
   CUFFT_TRY(c, cufftSetStream(c->c2r, c->st));
-  if (o->precond == 1) TRY(tl_setup(c));
+  if (o->precond == 1 || (o->precond == 2 && grid_div4(c))) TRY(tl_setup(c));
   TRY(tl_set_streams(c));
   c->have_eval = false;
   c->tl_image = false;
@@ -1469,7 +1474,7 @@ claire_status claire_precondition(claire_ctx* c, const float* r, float* z, int* 
   ENTER(c);
   if (!c || !r || !z) return CLAIRE_EINVAL;
   if (inner_iters) *inner_iters = 0;
-  if (c->opt.precond == 0) {
+  if (!two_level(c)) {
     TRY(spectral(c, CLAIRE_OP_REG_INV, r, z, c->beta_v));
   } else {
     if (!c->have_eval)

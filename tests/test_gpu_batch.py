@@ -85,7 +85,7 @@ def test_autotuner_picks_valid_shapes_and_keeps_results(claire):
     shape = SHAPES[2]
     m0, m1, _ = synth.blob_pair(shape, seed=8, kmax=3, max_disp_voxels=2.0)
     with claire.Context(shape, nt=4, beta_v=1e-2, max_newton=2, max_pcg=8,
-                        fixed_iters=1) as ctx:
+                        fixed_iters=1, precond=0) as ctx:
         ctx.set_images(dev(m0), dev(m1))
         v0, _ = ctx.solve()
         sl_t1, march_t1 = ctx.autotune()

@@ -98,7 +98,7 @@ def test_mixed_images_far_from_unit_range_are_scaled(claire):
 def test_mixed_two_gauss_newton_by_ten_pcg_against_oracle(claire):
     m0, m1, _ = synth.blob_pair(CUBE, seed=1)
     with claire.Context(CUBE, nt=4, beta_v=1e-2, max_newton=2, max_pcg=10, fixed_iters=1,
-                        precision=1) as ctx:
+                        precision=1, precond=0) as ctx:
         ctx.set_images(dev(m0), dev(m1))
         v, st = ctx.solve()
     prob = OR.Problem(f64(m0), f64(m1), 4, 1e-2)

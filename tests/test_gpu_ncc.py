@@ -71,7 +71,7 @@ def test_ncc_solve_matches_oracle(claire):
     m0, m1, _ = synth.blob_pair(shape, seed=3, kmax=3, max_disp_voxels=2.0)
     beta = 1e-4
     with claire.Context(shape, nt=4, beta_v=beta, distance=1, max_newton=2, max_pcg=5,
-                        fixed_iters=1) as ctx:
+                        fixed_iters=1, precond=0) as ctx:
         ctx.set_images(dev(m0), dev(m1))
         v, st = ctx.solve()
     prob = OR.Problem(_f64(m0), _f64(m1), 4, beta, distance="ncc")

@@ -205,7 +205,7 @@ def test_full_newton_solve_matches_oracle(claire):
     shape = (32, 32, 32)
     m0, m1, _ = _pair(shape, seed=7, kmax=3, disp=1.5)
     with claire.Context(shape, nt=4, beta_v=1e-2, max_newton=2, max_pcg=5, fixed_iters=1,
-                        hessian=1) as ctx:
+                        hessian=1, precond=0) as ctx:
         ctx.set_images(dev(m0), dev(m1))
         v, st = ctx.solve()
     prob = OR.Problem(_f64(m0), _f64(m1), 4, 1e-2)
@@ -234,7 +234,7 @@ def test_two_gauss_newton_by_ten_pcg_on_the_64_cube_matches_oracle(claire):
     """The parity workload: 64^3 blobs, nt 4, beta_v 1e-2, 2 GN x 10 PCG."""
     m0, m1, _ = synth.blob_pair(CUBE, seed=1)
     with claire.Context(CUBE, nt=4, beta_v=1e-2, max_newton=2, max_pcg=10,
-                        fixed_iters=1) as ctx:
+                        fixed_iters=1, precond=0) as ctx:
         ctx.set_images(dev(m0), dev(m1))
         v, st = ctx.solve()
     prob = OR.Problem(_f64(m0), _f64(m1), 4, 1e-2)

@@ -162,5 +162,23 @@ def test_two_level_errors(claire):
             ctx.set_options(precond=1)
         assert e.value.status == claire.EINVAL
         with pytest.raises(claire.ClaireError) as e:
-            ctx.set_options(precond=2)
+            ctx.set_options(precond=3)
         assert e.value.status == claire.EINVAL
+        ctx.set_options(precond=2)                        # automatic: spectral here
+
+
+def test_automatic_preconditioner_is_the_default(claire):
+    """options.precond = 2 (the default) is the two-level preconditioner on grids whose
+    sizes are multiples of 4 and the spectral one otherwise."""
+    for shape, expect_two_level in (((32, 32, 32), True), ((34, 32, 32), False)):
+        m0, m1, vt, r = _setup(shape)
+        with claire.Context(shape, nt=4, beta_v=1e-3) as ctx:
+            assert ctx.opts.precond == 2
+            ctx.set_images(dev(m0), dev(m1))
+            ctx.objective_gradient(dev(vt), want_gradient=False)
+            z, its = ctx.precondition(dev(r))
+            ref = ctx.spectral(claire.OP_REG_INV, dev(r))
+        if expect_two_level:
+            assert its > 0 and rel(host(z), host(ref)) > 1e-2
+        else:
+            assert its == 0 and rel(host(z), host(ref)) < 1e-6

@@ -37,7 +37,7 @@ def test_beta_search_follows_the_rule_and_matches_oracle(claire):
     shape = (16, 16, 16)
     m0, m1, _ = synth.blob_pair(shape, seed=5, kmax=2, max_disp_voxels=2.5)
     eps_d, rtol, nb = 0.5, 0.2, 4
-    with claire.Context(shape, nt=4, beta_v=1.0) as ctx:
+    with claire.Context(shape, nt=4, beta_v=1.0, precond=0) as ctx:
         ctx.set_images(dev(m0), dev(m1))
         beta, v, trials, st = ctx.beta_search(eps_d=eps_d, rtol=rtol, max_bisect=nb)
     assert beta > 0.0 and len(trials) >= 3 and st.newton_iters > 0
