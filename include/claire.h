@@ -278,7 +278,8 @@ claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
  *
  * Forward: y = act(conv(x, w) + bias); act = ReLU when relu != 0.  cin and cout
  * multiples of 16; y_bf16 ([V][cout] BF16) and / or y_f32 ([V][cout]) may be
- * NULL (not both); bias ([cout]) may be NULL. */
+ * NULL (not both); bias ([cout]) may be NULL.  V < 2^31 (EINVAL otherwise, here
+ * and for the weight gradient). */
 claire_status claire_conv3d_forward(const void* x, int B, int D, int H, int W, int cin,
                                     const void* w, const float* bias, int cout, int relu,
                                     void* y_bf16, float* y_f32, void* stream);

@@ -6,7 +6,8 @@
 // x-fastest spatial order as the registration fields), weights BF16
 // [Cout][27][Cin], accumulation FP32.  Convolutions are 3x3x3 with periodic
 // padding (the images live on a periodic grid) and run as implicit GEMMs on
-// the tensor cores (mma.sync m16n8k16 BF16 -> FP32):
+// the tensor cores (forward and data gradient: tcgen05 kind::f16 with the
+// accumulator in TMEM; weight gradient: mma.sync m16n8k16 BF16 -> FP32):
 //   forward  Y[v][n]  = sum_{t, c} W[n][t][c] X[nbr_t(v)][c]          (M = V, N = Cout, K = 27 Cin)
 //   dgrad    dX[v][c] = sum_{t, n} W[n][26 - t][c] dY[nbr_t(v)][n]   (forward with flipped weights)
 //   wgrad    dW[n][t][c] = sum_v dY[v][n] X[nbr_t(v)][c]              (M = Cout, N = Cin, K = V)
@@ -18,7 +19,9 @@
 #include <vector>
 
 #include "../../include/claire.h"
+#include "common.cuh"
 #include "reduce.cuh"
+#include "tc_sm100.cuh"
 
 namespace claire {
 namespace {
@@ -41,87 +44,174 @@ struct Vol {
   int B, D, H, W;
 };
 
-// Neighbour of voxel v at offset (dz, dy, dx) with periodic wrap inside its sample.
-__device__ __forceinline__ int64_t nbr(const Vol& s, int64_t v, int dz, int dy, int dx) {
-  int x = (int)(v % s.W);
-  int64_t r = v / s.W;
-  int y = (int)(r % s.H);
+// Voxel coordinates (batch, z, y, x) of a linear index (the volume of one call has
+// fewer than 2^31 voxels, so 32-bit divisions suffice), computed once per voxel.
+struct Vox {
+  int b, z, y, x;
+};
+__device__ __forceinline__ Vox vox_of(const Vol& s, int v) {
+  Vox o;
+  o.x = v % s.W;
+  int r = v / s.W;
+  o.y = r % s.H;
   r /= s.H;
-  int z = (int)(r % s.D);
-  const int64_t b = r / s.D;
-  x += dx; x = x < 0 ? x + s.W : (x >= s.W ? x - s.W : x);
-  y += dy; y = y < 0 ? y + s.H : (y >= s.H ? y - s.H : y);
-  z += dz; z = z < 0 ? z + s.D : (z >= s.D ? z - s.D : z);
-  return ((b * s.D + z) * s.H + y) * s.W + x;
+  o.z = r % s.D;
+  o.b = r / s.D;
+  return o;
+}
+
+// Neighbour at offset (dz, dy, dx) with periodic wrap inside its sample.
+__device__ __forceinline__ int nbr_of(const Vol& s, const Vox& p, int dz, int dy, int dx) {
+  int x = p.x + dx, y = p.y + dy, z = p.z + dz;
+  x = x < 0 ? x + s.W : (x >= s.W ? x - s.W : x);
+  y = y < 0 ? y + s.H : (y >= s.H ? y - s.H : y);
+  z = z < 0 ? z + s.D : (z >= s.D ? z - s.D : z);
+  return ((p.b * s.D + z) * s.H + y) * s.W + x;
 }
 
 // ------------------------------------------------------------------ forward / dgrad
 
-// CTA: 4 warps x 16 voxels = 64 output voxels, NT output channels (blockIdx.y
-// selects the channel tile).  K loop: 27 taps x Cin / 16 channel chunks.  A
-// fragments come straight from the channels-last activations (a channel pair
-// is one 32-bit word), B fragments from the weights (L1 / L2 resident).
-template <int NT>
+// Implicit-GEMM convolution on the fifth-generation tensor cores (tcgen05):
+// a CTA of 128 threads owns M = 128 consecutive output voxels and N output
+// channels; the FP32 accumulator D[128][N] lives in TMEM.  The K loop runs over
+// the 27 taps x Cin channels in stages of KC chunks of 16 channels of one tap
+// (channel groups outer, taps inner, so the activation rows a CTA re-reads for
+// the 27 taps stay in L1: the gathers use cp.async.ca):
+// every thread gathers its own voxel's neighbour row (cp.async, 16 bytes at a
+// time) and a share of the weight rows into shared memory in the no-swizzle
+// K-major core-matrix layout, then one thread issues the stage's kind::f16
+// MMAs (M = 128, N, K = 16 each) and commits them to the stage's mbarrier.
+// Four stage buffers, gathers issued two stages ahead (cp.async groups): the
+// gathers of stages i + 1 and i + 2 are in flight while stage i is waited for
+// and multiplied, and a buffer is refilled only after the mbarrier reports the
+// MMAs of its previous use done.  The epilogue reads the thread's TMEM lane (its
+// voxel) 16 columns at a time, adds the bias, applies the ReLU and stores BF16
+// and / or FP32.  Every wait is bounded; one that runs out makes the outputs NaN
+// instead of hanging.
+constexpr int CONV_M = 128;
+constexpr int CONV_S = 4;                         // stage buffers
+constexpr int CONV_L = 2;                         // stages gathered ahead
+constexpr uint32_t CONV_WAIT = 1u << 22;          // try_wait calls of <= 1 us each
+constexpr int CONV_STAGE_BYTES = 24 * 1024;       // shared memory per stage
+
+template <int N, int KC>
+struct ConvSmem {
+  static constexpr int A = KC * CONV_M * 32;       // bytes of A per stage
+  static constexpr int B = KC * N * 32;            // bytes of B per stage
+  static constexpr int bytes = CONV_S * (A + B);
+};
+
+template <int N, int KC>
 __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, Vol s, int Cin,
                                                   const bf16* __restrict__ Wt,
                                                   const float* __restrict__ bias, int Cout,
                                                   int relu, bf16* __restrict__ Y,
                                                   float* __restrict__ Y32) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, q = lane & 3;
+  using SM = ConvSmem<N, KC>;
+  constexpr uint32_t NCOL = N < 32 ? 32 : N;
+  extern __shared__ __align__(128) uint8_t conv_smem[];
+  __shared__ __align__(8) uint64_t mbar[CONV_S];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int n0 = blockIdx.y * N;
   const int64_t V = (int64_t)s.B * s.D * s.H * s.W;
-  const int64_t m0 = (int64_t)blockIdx.x * 64 + warp * 16;
-  const int n0 = blockIdx.y * NT;
-  const int64_t r0 = m0 + g, r1 = m0 + g + 8;
-  const int64_t v0 = r0 < V ? r0 : 0, v1 = r1 < V ? r1 : 0;
-  float acc[NT / 8][4];
+  const int64_t v = (int64_t)blockIdx.x * CONV_M + tid;        // this thread's row / voxel
+  const bool rv = v < V;
+  const Vox p = vox_of(s, rv ? (int)v : 0);
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, NCOL);
+    tmem_relinquish();
+  }
+  if (tid == 0)
+    for (int k = 0; k < CONV_S; ++k) mbar_init(&mbar[k], 1);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = umma_idesc_bf16(CONV_M, N);
+  const int chunks = Cin >> 4;                                 // 16-channel chunks per tap
+  const int per_tap = (chunks + KC - 1) / KC;                  // stages per tap
+  const int nstage = 27 * per_tap;
+  // issue the gathers of stage i into its buffer (one cp.async group)
+  auto gather = [&](int i) {
+    if (i < nstage) {
+      uint8_t* sa = conv_smem + (i % CONV_S) * (SM::A + SM::B);
+      uint8_t* sb = sa + SM::A;
+      const int t = i % 27, c_first = (i / 27) * KC;     // channel group outer, tap inner
+      const int kc_n = min(KC, chunks - c_first);
+      const bf16* xr =
+          X + (int64_t)nbr_of(s, p, t / 9 - 1, (t / 3) % 3 - 1, t % 3 - 1) * Cin + c_first * 16;
+      const int arow = (tid >> 3) * 128 + (tid & 7) * 16;
+      for (int kc = 0; kc < kc_n; ++kc)
 #pragma unroll
-  for (int j = 0; j < NT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  const int cw = Cin >> 1;                                     // 32-bit words per voxel
-  for (int t = 0; t < 27; ++t) {
-    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-    const uint32_t* xa = reinterpret_cast<const uint32_t*>(X) + nbr(s, v0, dz, dy, dx) * cw;
-    const uint32_t* xb = reinterpret_cast<const uint32_t*>(X) + nbr(s, v1, dz, dy, dx) * cw;
-    for (int c = 0; c < Cin; c += 16) {
-      const int w = c >> 1;
-      uint32_t a[4];
-      a[0] = __ldg(xa + w + q);
-      a[1] = __ldg(xb + w + q);
-      a[2] = __ldg(xa + w + 4 + q);
-      a[3] = __ldg(xb + w + 4 + q);
-#pragma unroll
-      for (int j = 0; j < NT / 8; ++j) {
-        const uint32_t* wp =
-            reinterpret_cast<const uint32_t*>(Wt + ((int64_t)(n0 + j * 8 + g) * 27 + t) * Cin);
-        uint32_t b[2];
-        b[0] = __ldg(wp + w + q);
-        b[1] = __ldg(wp + w + 4 + q);
-        mma16816(acc[j], a, b);
+        for (int h = 0; h < 2; ++h) {
+          uint8_t* dst = sa + kc * (CONV_M * 32) + h * (CONV_M * 16) + arow;
+          if (rv) cp_async16_ca(dst, xr + kc * 16 + h * 8);
+          else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+      for (int j = tid; j < kc_n * 2 * N; j += 128) {
+        const int kc = j / (2 * N), r = j - kc * 2 * N;
+        const int n = r >> 1, h = r & 1;
+        cp_async16_ca(sb + kc * (N * 32) + h * (N * 16) + (n >> 3) * 128 + (n & 7) * 16,
+                      Wt + ((int64_t)(n0 + n) * 27 + t) * Cin + (c_first + kc) * 16 + h * 8);
       }
     }
-  }
-#pragma unroll
-  for (int j = 0; j < NT / 8; ++j) {
-    const int n = n0 + j * 8 + 2 * q;
-    const float b0 = bias ? bias[n] : 0.f, b1 = bias ? bias[n + 1] : 0.f;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t r = h ? r1 : r0;
-      if (r >= V) continue;
-      float y0 = acc[j][2 * h] + b0, y1 = acc[j][2 * h + 1] + b1;
-      if (relu) {
-        y0 = fmaxf(y0, 0.f);
-        y1 = fmaxf(y1, 0.f);
-      }
-      if (Y)
-        *reinterpret_cast<uint32_t*>(Y + r * Cout + n) =
-            pack_bf16(__float2bfloat16_rn(y0), __float2bfloat16_rn(y1));
-      if (Y32) {
-        Y32[r * Cout + n] = y0;
-        Y32[r * Cout + n + 1] = y1;
-      }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  bool ok = true;
+  for (int i = 0; i < CONV_L; ++i) gather(i);
+  for (int i = 0; i < nstage; ++i) {
+    const int j = i + CONV_L;                                  // stage to gather now
+    if (j < nstage && j >= CONV_S)                             // its buffer's previous MMAs
+      ok &= mbar_wait(&mbar[j % CONV_S], ((j - CONV_S) / CONV_S) & 1, CONV_WAIT);
+    gather(j);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(CONV_L) : "memory");   // stage i landed
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after_sync();
+      uint8_t* sa = conv_smem + (i % CONV_S) * (SM::A + SM::B);
+      uint8_t* sb = sa + SM::A;
+      const int kc_n = min(KC, chunks - (i / 27) * KC);
+      for (int kc = 0; kc < kc_n; ++kc)
+        umma_bf16(tmem, umma_smem_desc(sa + kc * (CONV_M * 32), CONV_M * 16, 128),
+                  umma_smem_desc(sb + kc * (N * 32), N * 16, 128), idesc,
+                  (i > 0 || kc > 0) ? 1u : 0u);
+      umma_commit(&mbar[i % CONV_S]);
     }
   }
+  ok &= mbar_wait(&mbar[(nstage - 1) % CONV_S], ((nstage - 1) / CONV_S) & 1, CONV_WAIT);
+  tc_fence_after_sync();
+#pragma unroll 1
+  for (int c = 0; c < N; c += 16) {
+    float y[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, y);
+    if (!rv) continue;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      float t = y[e] + (bias ? bias[n0 + c + e] : 0.f);
+      if (relu) t = fmaxf(t, 0.f);
+      y[e] = ok ? t : __int_as_float(0x7fc00000);
+    }
+    if (Y) {
+      uint32_t w[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        w[e] = pack_bf16(__float2bfloat16_rn(y[2 * e]), __float2bfloat16_rn(y[2 * e + 1]));
+      uint4* dst = reinterpret_cast<uint4*>(Y + v * Cout + n0 + c);
+      dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    if (Y32) {
+      float4* dst = reinterpret_cast<float4*>(Y32 + v * Cout + n0 + c);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        dst[e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
+    }
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NCOL);
 }
 
 // W' [Cin][27][Cout] = W [Cout][26 - t][Cin]: dgrad is the forward conv of dY with W'.
@@ -165,7 +255,7 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, 
       const int64_t xv = ok ? xs[e] : x_begin;
       ya[e] = ok ? dY[xv * Cout + n0 + g] : __float2bfloat16_rn(0.f);
       yb[e] = ok ? dY[xv * Cout + n0 + g + 8] : __float2bfloat16_rn(0.f);
-      nb[e] = nbr(s, xv, dz, dy, dx) * Cin;
+      nb[e] = (int64_t)nbr_of(s, vox_of(s, (int)xv), dz, dy, dx) * Cin;
     }
     uint32_t a[4];
     a[0] = pack_bf16(ya[0], ya[1]);
@@ -406,6 +496,42 @@ std::vector<ResamplePlan> g_resample_plans;
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+template <int N, int KC>
+void launch_conv_fwd_kc(dim3 grid, cudaStream_t st, const bf16* X, const Vol& s, int cin,
+                        const bf16* Wt, const float* bias, int cout, int relu, bf16* Y,
+                        float* Y32) {
+  constexpr int bytes = ConvSmem<N, KC>::bytes;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_conv_fwd<N, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return true;
+  }();
+  (void)attr;
+  k_conv_fwd<N, KC><<<grid, 128, bytes, st>>>(X, s, cin, Wt, bias, cout, relu, Y, Y32);
+}
+
+// K per stage: KC 16-channel chunks, as many as divide the tap's chunks while a
+// stage stays within CONV_STAGE_BYTES of shared memory (four stage buffers).
+// Measured at 64^3 x 4 samples: deeper stages win (48 -> 16: 613 / 671 / 723 us
+// for KC = 3 / 2 / 1).
+template <int N>
+void launch_conv_fwd(dim3 grid, cudaStream_t st, const bf16* X, const Vol& s, int cin,
+                     const bf16* Wt, const float* bias, int cout, int relu, bf16* Y, float* Y32) {
+  const int chunks = cin / 16;
+  const int kc_max = CONV_STAGE_BYTES / (CONV_M * 32 + N * 32);
+  int kc = 1;
+  for (int k = 4; k >= 1; --k)
+    if (k <= kc_max && chunks % k == 0) {
+      kc = k;
+      break;
+    }
+  switch (kc) {
+    case 4: launch_conv_fwd_kc<N, 4>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, Y32); break;
+    case 3: launch_conv_fwd_kc<N, 3>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, Y32); break;
+    case 2: launch_conv_fwd_kc<N, 2>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, Y32); break;
+    default: launch_conv_fwd_kc<N, 1>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, Y32); break;
+  }
+}
+
 }  // namespace
 }  // namespace claire
 
@@ -423,15 +549,19 @@ claire_status claire_conv3d_forward(const void* x, int B, int D, int H, int W, i
     return CLAIRE_EINVAL;
   const Vol s{B, D, H, W};
   const int64_t V = (int64_t)B * D * H * W;
-  const int nt = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);
-  const dim3 grid(blocks(V, 64), cout / nt);
+  if (V >= INT32_MAX) return CLAIRE_EINVAL;
+  const int nt = cout % 128 == 0 ? 128 : (cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16));
+  const dim3 grid(blocks(V, CONV_M), cout / nt);
   cudaStream_t st = (cudaStream_t)stream;
   const bf16* X = (const bf16*)x;
   const bf16* Wt = (const bf16*)w;
   bf16* Y = (bf16*)y_bf16;
-  if (nt == 64) k_conv_fwd<64><<<grid, 128, 0, st>>>(X, s, cin, Wt, bias, cout, relu, Y, y_f32);
-  else if (nt == 32) k_conv_fwd<32><<<grid, 128, 0, st>>>(X, s, cin, Wt, bias, cout, relu, Y, y_f32);
-  else k_conv_fwd<16><<<grid, 128, 0, st>>>(X, s, cin, Wt, bias, cout, relu, Y, y_f32);
+  switch (nt) {
+    case 128: launch_conv_fwd<128>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, y_f32); break;
+    case 64: launch_conv_fwd<64>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, y_f32); break;
+    case 32: launch_conv_fwd<32>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, y_f32); break;
+    default: launch_conv_fwd<16>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, y_f32); break;
+  }
   return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
 }
 
@@ -453,6 +583,7 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
     return CLAIRE_EINVAL;
   const Vol s{B, D, H, W};
   const int64_t V = (int64_t)B * D * H * W;
+  if (V >= INT32_MAX) return CLAIRE_EINVAL;
   int64_t chunk = (V + nsplit - 1) / nsplit;
   chunk = ((chunk + 63) / 64) * 64;
   const int ns = (int)((V + chunk - 1) / chunk);
