@@ -80,6 +80,13 @@ typedef struct {
   int distance;         /* 0: 1/2 ||m(1) - m1||^2 (default, eq. varopt-claire).  1: NCC,
                            1 - <m(1), m1>^2 / (||m1||^2 ||m(1)||^2) (Appendix), which
                            changes lam(1) and lam~(1); needs precision 0             */
+  int warm_check;       /* 1: in claire_solve* and claire_solve_batch a nonzero initial
+                           guess v0 is kept only if J(v0) <= J(0), the distance of the
+                           template (the regulariser vanishes at v = 0); otherwise the
+                           solve restarts from v = 0 (the fallback of a learned warm
+                           start).  An accepted v0's evaluation is the solver's first
+                           one, so the check costs no extra PDE solve unless it
+                           rejects.  Default 0                                        */
 } claire_options;
 
 typedef struct {
@@ -89,6 +96,7 @@ typedef struct {
   double seconds;       /* device time of the call (CUDA events)                    */
   int status;
   int inner_iters;      /* nested CG iterations of the two-level preconditioner       */
+  int warm_fallback;    /* 1: options.warm_check rejected the initial guess            */
 } claire_stats;
 
 /* Fill *opt with the defaults listed above.  EINVAL on NULL. */

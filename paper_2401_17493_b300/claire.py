@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("gnorm0", ctypes.c_double), ("autotune", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("precond", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("distance", ctypes.c_int)]
+                ("distance", ctypes.c_int), ("warm_check", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("gnorm0", ctypes.c_double),
                 ("detF_min", ctypes.c_double), ("detF_max", ctypes.c_double),
                 ("detF_mean", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("status", ctypes.c_int), ("inner_iters", ctypes.c_int)]
+                ("status", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("warm_fallback", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

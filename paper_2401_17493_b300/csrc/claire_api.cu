@@ -1072,6 +1072,65 @@ bool valid_dims(int nx, int ny, int nz) {
   return 3.0 * N < 2147483647.0;
 }
 
+// The distance of the template, dist(m0, m1): J at v = 0, where m(1) = m0 and the
+// regulariser vanishes (eq. varopt-claire; the NCC form of the Appendix).
+claire_status distance_at_zero(claire_ctx* c, double* out) {
+  const int64_t N = N_of(c);
+  *out = 0.0;
+  if (c->opt.distance == 1) {
+    double a = 0.0, b = 0.0, cc = 0.0;
+    TRY(reduce(c, N, c->m0, c->m1, RED_DOT, &a));
+    TRY(reduce(c, N, c->m1, nullptr, RED_SQ, &b));
+    TRY(reduce(c, N, c->m0, nullptr, RED_SQ, &cc));
+    if (b > 0.0 && cc > 0.0) *out = 1.0 - a * a / (b * cc);
+    return CLAIRE_OK;
+  }
+  double sq = 0.0;
+  TRY(reduce(c, N, c->m0, c->m1, RED_SQDIFF, &sq));
+  *out = 0.5 * (double)c->g.h1 * c->g.h2 * c->g.h3 * sq;
+  return CLAIRE_OK;
+}
+
+// options.warm_check: keep a nonzero initial guess only if J(v0) <= J(0).  The
+// state solve and J at v0 come first; an accepted guess then gets its adjoint
+// and gradient, which the first Gauss-Newton level reuses as its evaluation.
+// Without a given denominator the evaluation at v = 0 provides both
+// ||g(0)||_inf and J(0).
+static claire_status warm_start_check(claire_ctx* c, double* gnorm0, Counters& k,
+                                      claire_stats* out) {
+  double vmax = 0.0;
+  TRY(absmax3(c, c->v, &vmax));
+  if (vmax == 0.0) return CLAIRE_OK;
+  double J0 = 0.0;
+  if (*gnorm0 <= 0.0) {
+    const size_t b3 = 3 * N_of(c) * sizeof(float);
+    CUDA_TRY(c, cudaMemcpyAsync(c->vtrial, c->v, b3, cudaMemcpyDeviceToDevice, c->st));
+    CUDA_TRY(c, cudaMemsetAsync(c->v, 0, b3, c->st));
+    TRY(evaluate(c));
+    k.pde += 2;
+    TRY(absmax3(c, c->grad, gnorm0));
+    J0 = c->J;
+    std::swap(c->v, c->vtrial);
+    c->have_eval = false;
+  } else {
+    TRY(distance_at_zero(c, &J0));
+  }
+  launch_trace(c->g, c->v, c->df, nullptr, ht_of(c), c->st);
+  TRY(check_launch(c, "trace"));
+  TRY(state_solve(c, c->df));
+  TRY(objective(c, c->v, &c->J));
+  ++k.pde;
+  if (c->J > J0) {                                 // the guess raises the objective
+    CUDA_TRY(c, cudaMemsetAsync(c->v, 0, 3 * N_of(c) * sizeof(float), c->st));
+    out->warm_fallback = 1;
+    return CLAIRE_OK;
+  }
+  TRY(adjoint_and_gradient(c));
+  ++k.pde;
+  c->have_eval = true;
+  return CLAIRE_OK;
+}
+
 claire_status finish_stats(claire_ctx* c, claire_stats* st, const Counters& k, float ms,
                            claire_status s) {
   if (!st) return s;
@@ -1080,20 +1139,8 @@ claire_status finish_stats(claire_ctx* c, claire_stats* st, const Counters& k, f
   st->pde_solves = k.pde;
   st->linesearch_halvings = k.halvings;
   st->inner_iters = k.inner;
-  const int64_t N = N_of(c);
   double mis0 = 0.0;
-  if (c->opt.distance == 1) {                      // NCC distance of the template
-    double a = 0.0, b = 0.0, cc = 0.0;
-    if (reduce(c, N, c->m0, c->m1, RED_DOT, &a) == CLAIRE_OK &&
-        reduce(c, N, c->m1, nullptr, RED_SQ, &b) == CLAIRE_OK &&
-        reduce(c, N, c->m0, nullptr, RED_SQ, &cc) == CLAIRE_OK && b > 0.0 && cc > 0.0) {
-      mis0 = 1.0 - a * a / (b * cc);
-      if (mis0 > 0.0) st->mismatch_rel = c->dist / mis0;
-    }
-  } else if (reduce(c, N, c->m0, c->m1, RED_SQDIFF, &mis0) == CLAIRE_OK && mis0 > 0.0) {
-    const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
-    st->mismatch_rel = c->dist / (0.5 * h3 * mis0);
-  }
+  if (distance_at_zero(c, &mis0) == CLAIRE_OK && mis0 > 0.0) st->mismatch_rel = c->dist / mis0;
   st->seconds = ms * 1e-3;
   st->status = (int)s;
   return s;
@@ -1122,6 +1169,7 @@ claire_status claire_default_options(claire_options* o) {
   o->max_inner = 50;
   o->inner_rtol = 0.0;
   o->distance = 0;
+  o->warm_check = 0;
   o->gnorm0 = 0.0;
   o->autotune = 0;
   o->graphs = 0;
@@ -1239,7 +1287,7 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
       !(o->beta_w >= 0.0) || !(o->eps_opt > 0.0) || o->max_newton < 0 || o->max_pcg < 1 ||
       o->forcing < 0 || o->forcing > 1 || o->precond < 0 || o->precond > 2 ||
       (o->precond != 0 && o->max_inner < 1) || !std::isfinite(o->inner_rtol) ||
-      o->distance < 0 || o->distance > 1)
+      o->distance < 0 || o->distance > 1 || o->warm_check < 0 || o->warm_check > 1)
     return fail(c, CLAIRE_EINVAL, "invalid option value");
   if (o->distance == 1 && o->precision != 0)
     return fail(c, CLAIRE_EINVAL, "the NCC distance needs FP32 storage (precision 0)");
@@ -1376,6 +1424,7 @@ static claire_status solve_levels(claire_ctx* c, const double* betas, int nlev, 
   for (int i = 0; i < nlev; ++i) {
     if (betas[i] != c->beta_v) drop_graphs(c);
     c->beta_v = betas[i];
+    if (i == 0 && c->opt.warm_check) TRY(warm_start_check(c, &gnorm0, k, out));
     s = gauss_newton(c, gnorm0, k, out);
     gnorm0 = out->gnorm0;
     if (s != CLAIRE_OK && s != CLAIRE_ENOTCONV) break;

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __
 //         c(x) with which one RK2 step of d_t lam = lam div v along -v becomes
 //         lam^j(x) = c(x) lam^{j+1}(y).
 template <int MODE>
-__global__ void __launch_bounds__(BRICK_THREADS) k_sl(Grid g, const float* __restrict__ u,
+__global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl(Grid g, const float* __restrict__ u,
                                                       const float* __restrict__ d,
                                                       const float* __restrict__ scale,
                                                       float sigma,
@@ -129,6 +129,9 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl(Grid g, const float* __res
   for (int k = 0; k < kmax; ++k) {
     const int i1 = i1_0 + k;
     const int64_t idx = idx0 + k * s1;
+    // the epilogue operands are requested before the gather, which hides their latency
+    const float sc = MODE == 0 && scale ? __ldg(scale + idx) : sigma;
+    const float ax = MODE == 0 && aux ? __ldg(aux + idx) : 0.0f;
     NodeTaps t;
     node_taps(dn[0], dn[1], dn[2], t);
     if (k + 1 < kmax) {
@@ -142,8 +145,8 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl(Grid g, const float* __res
       const float x = sm[ctr + k * BB2 * BB3];
       r = 1.0f + 0.5f * ht * (y + x + ht * x * y);
     } else {
-      r = y * (scale ? scale[idx] : sigma);
-      if (aux) r = fmaf(beta, aux[idx], r);
+      r = y * sc;
+      if (aux) r = fmaf(beta, ax, r);
     }
     out[idx] = r;
   }

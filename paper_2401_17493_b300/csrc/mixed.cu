@@ -105,7 +105,7 @@ __device__ __forceinline__ float gather_global_h(const __half* __restrict__ u, c
 }
 
 // out = (scale ? scale(x) : sigma) u(x + d) + beta aux(x), u / aux / out in FP16.
-__global__ void __launch_bounds__(BRICK_THREADS) k_sl_h(Grid g, const __half* __restrict__ u,
+__global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl_h(Grid g, const __half* __restrict__ u,
                                                         const float* __restrict__ d,
                                                         const float* __restrict__ scale,
                                                         float sigma,
@@ -130,6 +130,9 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl_h(Grid g, const __half* __
   for (int k = 0; k < kmax; ++k) {
     const int i1 = i1_0 + k;
     const int64_t idx = idx0 + k * s1;
+    // the epilogue operands are requested before the gather, which hides their latency
+    const float sc = scale ? __ldg(scale + idx) : sigma;
+    const float ax = aux ? __half2float(aux[idx]) : 0.0f;
     NodeTaps t;
     node_taps(dn[0], dn[1], dn[2], t);
     if (k + 1 < kmax) {
@@ -138,8 +141,8 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_sl_h(Grid g, const __half* __
     }
     const float y = taps_in_brick(t) ? gather_brick(smf, t, k, ty, lane)
                                      : gather_global_h(u, g, t, i1, i2, i3);
-    float r = y * (scale ? scale[idx] : sigma);
-    if (aux) r = fmaf(beta, __half2float(aux[idx]), r);
+    float r = y * sc;
+    if (aux) r = fmaf(beta, ax, r);
     out[idx] = __float2half_rn(r);
   }
 }

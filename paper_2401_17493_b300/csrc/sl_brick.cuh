@@ -97,26 +97,33 @@ __device__ __forceinline__ bool taps_in_brick(const NodeTaps& t) {
 }
 
 // 64-tap sum from the staged brick; (k, ty, lane) is the node's tile position.
+// The contraction runs on packed FP32 pairs (fma.rn.f32x2 of the sm_100 family):
+// rows j = 0, 1 and j = 2, 3 of each x1 plane share one instruction per x3 tap,
+// the x2 weights are applied pairwise and the two halves are added at the end.
+// Same FP32 arithmetic as the scalar form, half the FMA instructions, another
+// summation order (a zero displacement still returns the node value exactly:
+// its weights are (0, 1, 0, 0) on every axis).
 __device__ __forceinline__ float gather_brick(const float* __restrict__ s, const NodeTaps& t, int k,
                                               int ty, int lane) {
   const float* b = s + ((k + HB_LO + t.p1 - 1) * BB2 + (ty + HB_LO + t.p2 - 1)) * BB3 +
                    (lane + HB3_LO + t.p3 - 1);
-  float acc = 0.0f;
+  const float2 w2a = make_float2(t.w2[0], t.w2[1]), w2b = make_float2(t.w2[2], t.w2[3]);
+  float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float acc2 = 0.0f;
+    const float* p = b + i * BB2 * BB3;            // row (i, j = 0); rows j are BB3 apart
+    float2 ra = make_float2(0.0f, 0.0f), rb = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float* row = b + (i * BB2 + j) * BB3;
-      float acc3 = t.w3[0] * row[0];
-      acc3 = fmaf(t.w3[1], row[1], acc3);
-      acc3 = fmaf(t.w3[2], row[2], acc3);
-      acc3 = fmaf(t.w3[3], row[3], acc3);
-      acc2 = fmaf(t.w2[j], acc3, acc2);
+    for (int c = 0; c < 4; ++c) {
+      const float2 w = make_float2(t.w3[c], t.w3[c]);
+      ra = __ffma2_rn(w, make_float2(p[c], p[BB3 + c]), ra);
+      rb = __ffma2_rn(w, make_float2(p[2 * BB3 + c], p[3 * BB3 + c]), rb);
     }
-    acc = fmaf(t.w1[i], acc2, acc);
+    float2 a2 = __fmul2_rn(w2a, ra);
+    a2 = __ffma2_rn(w2b, rb, a2);
+    acc = __ffma2_rn(make_float2(t.w1[i], t.w1[i]), a2, acc);
   }
-  return acc;
+  return acc.x + acc.y;
 }
 
 // Same 64-tap sum from global memory with periodic wrap (any displacement).

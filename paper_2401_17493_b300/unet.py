@@ -351,47 +351,123 @@ def train(model, inputs, targets, epochs, lr=5e-4, batch=4, seed=0, log=None, wa
     return hist
 
 
+def _predict_batch(model, pairs, n):
+    """Warm-start velocities of a list of (m0, m1) pairs on the n^3 grid: one batched
+    restriction of all images to 64^3, one network pass, one batched prolongation."""
+    import torch
+    B = len(pairs)
+    imgs = torch.stack([f for mm in pairs for f in mm]).contiguous()          # (2B, n, n, n)
+    small = resample(imgs, (n, n, n), (64, 64, 64), 2 * B).reshape(B, 2, 64, 64, 64)
+    v64 = model.predict([small[k] for k in range(B)], B)                     # (B, 3, 64^3)
+    v = resample(v64.reshape(3 * B, 64, 64, 64).contiguous(), (64, 64, 64), (n, n, n), 3 * B)
+    return list(v.reshape(B, 3, n, n, n))
+
+
 def evaluate(model, pairs, n, beta, eps_opt=5e-2):
-    """Zero-init vs warm-started solves (same tolerance and denominator)."""
+    """Zero-init vs warm-started solves of each pair, one pair at a time (same tolerance
+    and denominator).  The warm arm's cost includes the prediction; its J(v_pred) <= J(0)
+    test runs inside the solve (options.warm_check)."""
     import torch
     res = []
     for m0, m1 in pairs:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        small = resample(torch.stack([m0, m1]).contiguous(), (n, n, n), (64, 64, 64), 2)
-        v64 = model.predict([small], 1)[0]
-        v0 = resample(v64.contiguous(), (64, 64, 64), (n, n, n), 3).contiguous()
+        v0 = _predict_batch(model, [(m0, m1)], n)[0].clone()
         torch.cuda.synchronize()
         t_pred = time.perf_counter() - t0
         with C.Context((n, n, n), nt=4, beta_v=beta, eps_opt=eps_opt, precond=PRECOND,
                        max_inner=MAX_INNER) as ctx:
             ctx.set_images(m0, m1)
             z = torch.zeros((3, n, n, n), device="cuda")
-            # J(0) and |g(0)| are shared by both arms (the same stopping test);
-            # the check J(v_pred) <= J(0) belongs to the warm arm's cost
-            J0, g0 = ctx.objective_gradient(z)
-            gnorm0 = float(g0.abs().max())
+            # |g(0)| is shared by both arms (the same stopping test)
+            _, g0 = ctx.objective_gradient(z)
+            ctx.set_options(gnorm0=float(g0.abs().max()))
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            Jp, _ = ctx.objective_gradient(v0, want_gradient=False)
-            fallback = Jp > J0
-            t_pred += time.perf_counter() - t0
-            ctx.set_options(gnorm0=gnorm0)
             t0 = time.perf_counter()
             vz, sz = ctx.solve(torch.zeros_like(z))
             torch.cuda.synchronize()
             tz = time.perf_counter() - t0
+            ctx.set_options(warm_check=1)
             t0 = time.perf_counter()
-            vw, sw = ctx.solve(torch.zeros_like(z) if fallback else v0.clone())
+            vw, sw = ctx.solve(v0)
             torch.cuda.synchronize()
             tw = time.perf_counter() - t0 + t_pred      # the prediction is part of the cost
         res.append({"t_zero": tz, "t_warm": tw, "t_predict": t_pred, "matvecs_zero": sz.matvecs,
                     "matvecs_warm": sw.matvecs, "newton_zero": sz.newton_iters,
                     "newton_warm": sw.newton_iters, "grad_rel_zero": sz.grad_rel,
                     "grad_rel_warm": sw.grad_rel, "mismatch_zero": sz.mismatch_rel,
-                    "mismatch_warm": sw.mismatch_rel, "fallback": bool(fallback),
-                    "J_pred_over_J0": Jp / J0})
+                    "mismatch_warm": sw.mismatch_rel, "fallback": bool(sw.warm_fallback)})
     return res
+
+
+def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
+    """The plain method against the combined form on the same pairs.
+
+    plain:    FP32 storage, zero initial guess, one pair after the other;
+    combined: mixed precision (FP16 field storage), U-Net warm start with the
+              J(v_pred) <= J(0) fallback inside the solver (options.warm_check), and
+              the pairs of a chunk solved concurrently by claire_solve_batch with
+              graph-captured PCG iterations.
+    Both arms stop at the same relative gradient with the same denominator
+    |g(0)|_inf (from the FP32 context); context creation and g(0) are outside both
+    timings, the prediction (batched restriction, network, prolongation) is inside
+    the combined one."""
+    import torch
+    out = {"t_plain": 0.0, "t_combined": 0.0, "t_predict": 0.0, "t_solve_batch": 0.0,
+           "matvecs_plain": [], "matvecs_combined": [], "mismatch_plain": [],
+           "mismatch_combined": [], "grad_rel_plain": [], "grad_rel_combined": [],
+           "fallbacks": 0}
+    opts = dict(nt=4, beta_v=beta, eps_opt=eps_opt, precond=PRECOND, max_inner=MAX_INNER)
+    for c0 in range(0, len(pairs), batch):
+        chunk = pairs[c0:c0 + batch]
+        plain = [C.Context((n, n, n), **opts) for _ in chunk]
+        comb = [C.Context((n, n, n), precision=1, graphs=1, warm_check=1, **opts)
+                for _ in chunk]
+        for (m0, m1), cp, cc in zip(chunk, plain, comb):
+            cp.set_images(m0, m1)
+            cc.set_images(m0, m1)
+            _, g0 = cp.objective_gradient(torch.zeros((3, n, n, n), device="cuda"))
+            gnorm0 = float(g0.abs().max())
+            cp.set_options(gnorm0=gnorm0)
+            cc.set_options(gnorm0=gnorm0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for cp in plain:
+            _, st = cp.solve(torch.zeros((3, n, n, n), device="cuda"))
+            out["matvecs_plain"].append(st.matvecs)
+            out["mismatch_plain"].append(st.mismatch_rel)
+            out["grad_rel_plain"].append(st.grad_rel)
+        torch.cuda.synchronize()
+        out["t_plain"] += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        v0s = [v.clone() for v in _predict_batch(model, chunk, n)]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, stats = C.solve_batch(comb, v0s)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out["t_predict"] += t1 - t0
+        out["t_solve_batch"] += t2 - t1
+        out["t_combined"] += t2 - t0
+        for st in stats:
+            out["matvecs_combined"].append(st.matvecs)
+            out["mismatch_combined"].append(st.mismatch_rel)
+            out["grad_rel_combined"].append(st.grad_rel)
+            out["fallbacks"] += st.warm_fallback
+        for c in plain + comb:
+            c.close()
+    npairs = len(pairs)
+    summ = {"pairs": npairs, "batch": batch,
+            "t_plain_per_pair": out["t_plain"] / npairs,
+            "t_combined_per_pair": out["t_combined"] / npairs,
+            "t_predict_per_pair": out["t_predict"] / npairs,
+            "t_solve_batch_per_pair": out["t_solve_batch"] / npairs,
+            "speedup": out["t_plain"] / out["t_combined"], "fallbacks": out["fallbacks"]}
+    for k in ("matvecs", "mismatch", "grad_rel"):
+        for arm in ("plain", "combined"):
+            summ[f"mean_{k}_{arm}"] = float(np.mean(out[f"{k}_{arm}"]))
+    summ["max_grad_rel"] = float(max(out["grad_rel_plain"] + out["grad_rel_combined"]))
+    return summ
 
 
 def main():
@@ -405,6 +481,9 @@ def main():
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--precond", type=int, default=PRECOND,
                     help="registration preconditioner: 0 spectral, 1 two-level")
+    ap.add_argument("--combined-batch", type=int, default=16,
+                    help="pairs per concurrent batch in the plain-vs-combined comparison "
+                         "(0 skips it)")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     globals()["PRECOND"] = args.precond
@@ -449,6 +528,10 @@ def main():
     summary["speedup_time"] = summary["mean_t_zero"] / summary["mean_t_warm"]
     summary["speedup_matvecs"] = summary["mean_matvecs_zero"] / max(1e-9, summary["mean_matvecs_warm"])
     log(json.dumps(summary))
+    if args.combined_batch > 0:
+        summary["combined"] = evaluate_combined(model, make_pairs(eval_seeds, n), n, args.beta,
+                                                batch=args.combined_batch)
+        log("plain vs combined: " + json.dumps(summary["combined"]))
     if args.out:
         with open(args.out, "w") as f:
             json.dump({"summary": summary, "pairs": res}, f, indent=1)

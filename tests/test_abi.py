@@ -59,3 +59,34 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     o = claire.Options()
     assert lib.claire_default_options(ctypes.byref(o)) == claire.OK
     assert abs(o.eps_opt - 5e-2) < 1e-15 and o.max_pcg == 100 and o.hessian == 0
+    assert o.precond == 2 and o.warm_check == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of claire_options, claire_stats and claire_kernel_stat
+    have the header's size and field offsets (a C program compiled with gcc
+    against include/claire.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_2401_17493_b300 import claire
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    mirrors = {"claire_options": claire.Options, "claire_stats": claire.Stats,
+               "claire_kernel_stat": claire.KernelStat}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "claire.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out.splitlines())}
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
