@@ -44,7 +44,7 @@ INTERP_FD = ("trace", "sl_step", "adjoint_factor", "grad8", "div8", "sdot_hist",
 # dram__bytes_write.sum) for the kernels below, from the capture summarised in
 # profiles/k_sl_256cube.md (matvec SL steps, 24 algorithmic B/voxel); drop an
 # entry when its kernel changes.
-NCU_TRAFFIC_PER_VOXEL = {"sl_step": 23.27}
+NCU_TRAFFIC_PER_VOXEL = {"sl_step": 23.25}
 
 
 def parse():

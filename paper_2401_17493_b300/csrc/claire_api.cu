@@ -87,6 +87,13 @@ struct claire_ctx {
   bool tl_ready = false, tl_image = false;
   double tl_rtol = 1e-3;        // nested CG relative tolerance of the current PCG
   int tl_iters = 0;             // nested CG iterations not yet counted in the stats
+  // the nested CG as a conditional while node in captured PCG parts: the stream its
+  // body is captured on, the launches of one body replay, and whether capturing it
+  // failed (part B then runs launch by launch)
+  cudaStream_t tl_body = nullptr;
+  long long tl_body_launches[K_COUNT] = {};
+  double tl_body_bytes[K_COUNT] = {};
+  bool tl_nograph = false;
   cudaStream_t own = nullptr;   // private stream for graph capture
   cudaStream_t user = nullptr;  // the stream of the options
   cudaEvent_t e_in = nullptr;   // orders the private stream after the user's stream
@@ -228,7 +235,11 @@ bool two_level(const claire_ctx* c) {
 // Slots of the device-side FP64 scalars.
 enum { SLOT_RZ0 = 0, SLOT_RZ1 = 1, SLOT_SHS = 2, SLOT_RR = 3, SLOT_MEAN = 4, SLOT_VMAX = 8,
        SLOT_TL_RR0 = 9, SLOT_TL_RR1 = 10, SLOT_TL_PAP = 11, SLOT_ZERO = 12 /* ..14 */,
-       SLOT_NCC_AL = 15, SLOT_NCC_GA = 16, NSLOTS = 24 };
+       SLOT_NCC_AL = 15, SLOT_NCC_GA = 16,
+       // nested CG on the device (captured PCG part B): relative tolerance, stop
+       // threshold, iterations of the current application, iterations since PCG start
+       SLOT_TL_RTOL = 17, SLOT_TL_STOP = 18, SLOT_TL_COUNT = 19, SLOT_TL_ITS = 20,
+       NSLOTS = 24 };
 
 // Power-of-two scale that maps max(|m0|, |m1|) into (1/2, 1] (FP16 state range).
 claire_status image_scale(claire_ctx* c) {
@@ -643,6 +654,88 @@ claire_status tl_update_image(claire_ctx* c) {
 // (I + R^-1/2 (grad m_c (x) grad m_c) R^-1/2) s_c = t_c; s_c is prolonged, the
 // high modes are kept, and R^-1/2 is applied again.  With rz_slot >= 0, <r, z>
 // goes to slots[rz_slot].
+// The nested CG of the two-level preconditioner inside the graph being captured on
+// c->st (options.graphs): k_tl_cg_begin sets the condition of a while node whose
+// body is one CG iteration ending in k_tl_cg_control, so the loop runs on the
+// device with the host loop's stopping decisions and no host round trip.  The
+// residual slots keep fixed roles (rr in SLOT_TL_RR0, the new one in SLOT_TL_RR1,
+// copied back by the control kernel); an iteration's direction update also runs
+// after the last iteration, where p is no longer used.  The iterations of all
+// applications since the PCG start add up in SLOT_TL_ITS.
+claire_status tl_cg_graph(claire_ctx* c) {
+  const Grid& gc = c->gc;
+  const int64_t Ch = (int64_t)gc.n1 * gc.n2 * (gc.n3 / 2 + 1);
+  const double fft_c = 3.0 * (4.0 * gc.N + 8.0 * Ch);
+  const float inv_nc = (float)(1.0 / (double)gc.N);
+  if (!c->tl_body) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->tl_body, cudaStreamNonBlocking));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CUDA_TRY(c, cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphConditionalHandle h;
+  CUDA_TRY(c, cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
+  double* sl = c->slots;
+  launch_tl_cg_begin(h, sl + SLOT_TL_RR0, sl + SLOT_TL_RTOL, sl + SLOT_TL_STOP,
+                     sl + SLOT_TL_COUNT, c->opt.max_inner, c->st);
+  TRY(check_launch(c, "nested cg begin"));
+  CUDA_TRY(c, cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  CUDA_TRY(c, cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
+  CUDA_TRY(c, cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1,
+                                                  cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const cudaStream_t bs = c->tl_body;
+  Profiler* saved = tl_prof;
+  Profiler counter;                                 // launches of one iteration
+  tl_prof = &counter;
+  CUDA_TRY(c, cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+  auto iteration = [&]() -> claire_status {
+    CUFFT_TRY(c, cufftSetStream(c->tl_c2r3, bs));
+    CUFFT_TRY(c, cufftSetStream(c->tl_r2c3, bs));
+    launch_tl_spec_scale(gc, c->tl_fw, c->tl_sp, c->tl_cc, 1.0f, bs);
+    {
+      ProfileRange pr(K_CUFFT, fft_c, bs);
+      CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)c->tl_q));
+    }
+    launch_tl_outer(gc.N, c->tl_gm, c->tl_q, c->tl_w, bs);
+    {
+      ProfileRange pr(K_CUFFT, fft_c, bs);
+      CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)c->tl_w, c->tl_cc));
+    }
+    launch_tl_spec_finish(gc, c->tl_fw, c->tl_sp, c->tl_cc, c->tl_sap, inv_nc, c->partial,
+                          sl + SLOT_TL_PAP, bs);
+    launch_tl_spec_step(gc, c->tl_fw, sl + SLOT_TL_RR0, sl + SLOT_TL_PAP, c->tl_sx, c->tl_sr,
+                        c->tl_sp, c->tl_sap, c->partial, sl + SLOT_TL_RR1, bs);
+    launch_tl_cg_dir(6 * Ch, sl + SLOT_TL_RR1, sl + SLOT_TL_RR0, (const float*)c->tl_sr,
+                     (float*)c->tl_sp, bs);
+    launch_tl_cg_control(h, sl + SLOT_TL_RR0, sl + SLOT_TL_RR1, sl + SLOT_TL_PAP,
+                         sl + SLOT_TL_STOP, sl + SLOT_TL_COUNT, sl + SLOT_TL_ITS,
+                         c->opt.max_inner, bs);
+    return check_launch(c, "nested cg body");
+  };
+  claire_status s = iteration();
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(bs, &captured);
+  tl_prof = saved;
+  const claire_status s2 = tl_set_streams(c);      // the plans back on c->st
+  if (s != CLAIRE_OK) return s;
+  if (e != cudaSuccess)
+    return fail(c, CLAIRE_ECUDA, "nested cg body capture: %s", cudaGetErrorString(e));
+  if (s2 != CLAIRE_OK) return s2;
+  for (int k = 0; k < K_COUNT; ++k) {
+    c->tl_body_launches[k] = counter.launches[k];
+    c->tl_body_bytes[k] = counter.bytes[k];
+  }
+  return CLAIRE_OK;
+}
+
 claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz, int rz_slot) {
   TRY(tl_setup(c));
   if (!c->tl_image) return fail(c, CLAIRE_EORDER, "two-level preconditioner has no image");
@@ -667,6 +760,11 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
   launch_tl_spec_init(gc, c->tl_fw, c->tl_cc, c->tl_sx, c->tl_sr, c->tl_sp, c->partial,
                       c->slots + cur, c->st);
   TRY(check_launch(c, "nested cg"));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CUDA_TRY(c, cudaStreamIsCapturing(c->st, &cs));
+  if (cs == cudaStreamCaptureStatusActive) {
+    TRY(tl_cg_graph(c));
+  } else {
   CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->slots + cur, sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -704,6 +802,7 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
     std::swap(cur, nxt);
   }
   c->tl_iters += it;
+  }
   // prolong the coarse solution (already a spectrum), keep the high modes, R^-1/2
   launch_tl_merge(g, c->cbuf, c->tl_sx, c->cbuf2, alpha, gamma, (float)(1.0 / (double)N), 1.0f,
                   c->st);
@@ -812,9 +911,9 @@ void drop_graphs(claire_ctx* c) {
 // graph when options.graphs is set (captured on first use; the kernels inside
 // are counted per replay, not event-timed).
 claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
-  // the nested CG of the two-level preconditioner reads its residual on the
-  // host, so part B is not captured then
-  if (!c->opt.graphs || (which == 1 && two_level(c)))
+  // with the two-level preconditioner part B holds the nested CG as a conditional
+  // while node; if that capture is refused, part B runs launch by launch
+  if (!c->opt.graphs || (which == 1 && two_level(c) && c->tl_nograph))
     return which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
   const int slot = 4 * (c->df == c->dbuf0 ? 0 : 1) + 2 * which + (cur == SLOT_RZ0 ? 0 : 1);
   if (!c->graph_exec[slot]) {
@@ -826,14 +925,23 @@ claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
     claire_status s = which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
     cudaError_t e = cudaStreamEndCapture(c->st, &graph);
     tl_prof = saved;
-    if (s != CLAIRE_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return s;
+    if (s == CLAIRE_OK && e == cudaSuccess) {
+      e = cudaGraphInstantiate(&c->graph_exec[slot], graph, 0);
+      if (e != cudaSuccess) c->graph_exec[slot] = nullptr;
     }
+    if (graph) cudaGraphDestroy(graph);
+    if (which == 1 && two_level(c) && (s != CLAIRE_OK || e != cudaSuccess)) {
+      // nothing of the failed capture ran: run this part (and later ones) uncaptured
+      cudaGetLastError();
+      if (c->opt.verbose)
+        fprintf(stderr, "[claire] nested CG not captured (%s); PCG part B runs uncaptured\n",
+                c->err.empty() ? cudaGetErrorString(e) : c->err.c_str());
+      c->err.clear();
+      c->tl_nograph = true;
+      return pcg_part_b(c, cur, nxt);
+    }
+    if (s != CLAIRE_OK) return s;
     if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->graph_exec[slot], graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     for (int k = 0; k < K_COUNT; ++k) {
       c->graph_launches[slot][k] = counter.launches[k];
       c->graph_bytes[slot][k] = counter.bytes[k];
@@ -860,6 +968,21 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
   *curv = CLAIRE_OK;
   CUDA_TRY(c, cudaMemsetAsync(c->vt, 0, n3 * sizeof(float), c->st));
   CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
+  CUDA_TRY(c, cudaMemsetAsync(c->slots + SLOT_TL_ITS, 0, sizeof(double), c->st));
+  // nested CG iterations run by captured part-B graphs (a running total on the
+  // device): read with the slots after each part A, as every part B is followed
+  // by one, and counted with their launches
+  int graph_its = 0;
+  auto graph_inner = [&]() {
+    const int its = (int)c->hslots[SLOT_TL_ITS] - graph_its;
+    graph_its += its;
+    c->tl_iters += its;
+    if (tl_prof)
+      for (int kk = 0; kk < K_COUNT; ++kk) {
+        tl_prof->launches[kk] += (long long)its * c->tl_body_launches[kk];
+        tl_prof->bytes[kk] += its * c->tl_body_bytes[kk];
+      }
+  };
   launch_lincomb(n3, -1.0f, c->grad, 0.0f, c->grad, c->r, c->st);    // r = -g
   int cur = SLOT_RZ0;
   TRY(precondition(c, cur));
@@ -876,6 +999,7 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     const double sHs = c->hslots[SLOT_SHS], rr = c->hslots[SLOT_RR];
     const int flag = *(const int*)(c->hslots + NSLOTS);
+    graph_inner();
     if (flag) {
       if (!std::isfinite(sHs) || !std::isfinite(c->hslots[cur]))
         return fail(c, CLAIRE_ENONFINITE, "PCG scalar not finite");
@@ -1031,6 +1155,7 @@ claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_sta
       // H0 at the current m(1); nested tolerance a tenth of the outer one (Sec. 2.6)
       TRY(tl_update_image(c));
       c->tl_rtol = c->opt.inner_rtol > 0.0 ? c->opt.inner_rtol : 0.1 * eta;
+      launch_set_scalar(c->slots + SLOT_TL_RTOL, c->tl_rtol, c->st);   // for captured parts
       c->tl_iters = 0;
     }
     TRY(pcg(c, eta * std::sqrt(gg), k, &curv));
@@ -1181,6 +1306,7 @@ claire_status claire_destroy(claire_ctx* c) {
   c->prof.release();
   drop_graphs(c);
   if (c->own) cudaStreamDestroy(c->own);
+  if (c->tl_body) cudaStreamDestroy(c->tl_body);
   if (c->plans) {
     cufftDestroy(c->r2c);
     cufftDestroy(c->c2r);

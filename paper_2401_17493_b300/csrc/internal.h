@@ -126,6 +126,13 @@ void launch_tl_outer(int64_t n, const float* gm, const float* q, float* w, cudaS
 void launch_tl_cg_dir(int64_t n, const double* rr_new, const double* rr_old, const float* r,
                       float* p, cudaStream_t st);
 void launch_tl_unscale_h(int64_t n, const __half* h, float inv, float* out, cudaStream_t st);
+// Device-side control of the nested CG inside a graph with a conditional while node.
+void launch_tl_cg_begin(cudaGraphConditionalHandle h, const double* rr0, const double* rtol,
+                        double* stop2, double* count, int max_inner, cudaStream_t st);
+void launch_tl_cg_control(cudaGraphConditionalHandle h, double* rr, const double* rr_new,
+                          const double* pAp, const double* stop2, double* count, double* total,
+                          int max_inner, cudaStream_t st);
+void launch_set_scalar(double* p, double v, cudaStream_t st);
 int tl_spec_blocks(const Grid& gc);
 void launch_tl_spec_table(const Grid& gc, float alpha, float gamma, float2* fw, cudaStream_t st);
 void launch_tl_spec_scale(const Grid& gc, const float2* fw, const cufftComplex* in,

@@ -340,6 +340,57 @@ void launch_tl_spec_init(const Grid& gc, const float2* fw, const cufftComplex* b
   launch_reduce_final(partial, tl_spec_blocks(gc), RED_SUM, bb, st);
 }
 
+// ---- nested CG driven on the device (a captured graph with a conditional while
+// node): the same iteration and the same stopping decisions as the host loop of
+// the preconditioner, taken by one thread from the FP64 slots.
+
+// Before the loop: stop2 = rtol^2 <b, b>, iteration count 0, and whether to iterate.
+__global__ void k_tl_cg_begin(cudaGraphConditionalHandle h, const double* __restrict__ rr0,
+                              const double* __restrict__ rtol, double* __restrict__ stop2,
+                              double* __restrict__ count, int max_inner) {
+  const double r = *rr0, t = *rtol;
+  const double s2 = t * t * r;
+  *stop2 = s2;
+  *count = 0.0;
+  cudaGraphSetConditional(h, (max_inner > 0 && r > s2 && isfinite(r)) ? 1u : 0u);
+}
+
+// After an iteration (step, then direction): rr <- rr_new, count the iteration, and
+// continue only after a positive-curvature step that left the residual above the
+// tolerance, below the iteration cap.
+__global__ void k_tl_cg_control(cudaGraphConditionalHandle h, double* __restrict__ rr,
+                                const double* __restrict__ rr_new, const double* __restrict__ pAp,
+                                const double* __restrict__ stop2, double* __restrict__ count,
+                                double* __restrict__ total, int max_inner) {
+  const double q = *pAp, rn = *rr_new;
+  const double it = *count + 1.0;
+  *count = it;
+  *total += 1.0;
+  *rr = rn;
+  const bool go = q > 0.0 && isfinite(q) && rn > *stop2 && it < (double)max_inner;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_set_scalar(double* __restrict__ p, double v) { *p = v; }
+
+void launch_tl_cg_begin(cudaGraphConditionalHandle h, const double* rr0, const double* rtol,
+                        double* stop2, double* count, int max_inner, cudaStream_t st) {
+  ProfileRange pr(K_PRECOND, 32.0, st);
+  k_tl_cg_begin<<<1, 1, 0, st>>>(h, rr0, rtol, stop2, count, max_inner);
+}
+
+void launch_tl_cg_control(cudaGraphConditionalHandle h, double* rr, const double* rr_new,
+                          const double* pAp, const double* stop2, double* count, double* total,
+                          int max_inner, cudaStream_t st) {
+  ProfileRange pr(K_PRECOND, 56.0, st);
+  k_tl_cg_control<<<1, 1, 0, st>>>(h, rr, rr_new, pAp, stop2, count, total, max_inner);
+}
+
+void launch_set_scalar(double* p, double v, cudaStream_t st) {
+  ProfileRange pr(K_VECTOR, 8.0, st);
+  k_set_scalar<<<1, 1, 0, st>>>(p, v);
+}
+
 void launch_tl_unscale_h(int64_t n, const __half* h, float inv, float* out, cudaStream_t st) {
   ProfileRange pr(K_PRECOND, (double)n * 6, st);
   k_tl_unscale_h<<<vector_blocks(n), 256, 0, st>>>(n, h, inv, out);

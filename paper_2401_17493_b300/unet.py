@@ -406,67 +406,78 @@ def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
     plain:    FP32 storage, zero initial guess, one pair after the other;
     combined: mixed precision (FP16 field storage), U-Net warm start with the
               J(v_pred) <= J(0) fallback inside the solver (options.warm_check), and
-              the pairs of a chunk solved concurrently by claire_solve_batch with
-              graph-captured PCG iterations.
+              the pairs solved `batch` at a time by claire_solve_batch with
+              graph-captured PCG iterations; the prediction of the next batch runs
+              on a side stream while the current batch is solved.
     Both arms stop at the same relative gradient with the same denominator
-    |g(0)|_inf (from the FP32 context); context creation and g(0) are outside both
-    timings, the prediction (batched restriction, network, prolongation) is inside
-    the combined one."""
+    |g(0)|_inf (from an FP32 evaluation at v = 0).  Context creation and g(0) are
+    outside both timings; the combined time is the wall time from the first
+    prediction to the last solve."""
     import torch
-    out = {"t_plain": 0.0, "t_combined": 0.0, "t_predict": 0.0, "t_solve_batch": 0.0,
-           "matvecs_plain": [], "matvecs_combined": [], "mismatch_plain": [],
-           "mismatch_combined": [], "grad_rel_plain": [], "grad_rel_combined": [],
-           "fallbacks": 0}
     opts = dict(nt=4, beta_v=beta, eps_opt=eps_opt, precond=PRECOND, max_inner=MAX_INNER)
-    for c0 in range(0, len(pairs), batch):
-        chunk = pairs[c0:c0 + batch]
-        plain = [C.Context((n, n, n), **opts) for _ in chunk]
-        comb = [C.Context((n, n, n), precision=1, graphs=1, warm_check=1, **opts)
-                for _ in chunk]
-        for (m0, m1), cp, cc in zip(chunk, plain, comb):
+    res = {k: [] for k in ("matvecs_plain", "matvecs_combined", "mismatch_plain",
+                           "mismatch_combined", "grad_rel_plain", "grad_rel_combined")}
+    zeros = lambda: torch.zeros((3, n, n, n), device="cuda")
+    # plain arm, and the shared denominators
+    gnorm0s, t_plain = [], 0.0
+    for (m0, m1) in pairs:
+        with C.Context((n, n, n), **opts) as cp:
             cp.set_images(m0, m1)
-            cc.set_images(m0, m1)
-            _, g0 = cp.objective_gradient(torch.zeros((3, n, n, n), device="cuda"))
-            gnorm0 = float(g0.abs().max())
-            cp.set_options(gnorm0=gnorm0)
-            cc.set_options(gnorm0=gnorm0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for cp in plain:
-            _, st = cp.solve(torch.zeros((3, n, n, n), device="cuda"))
-            out["matvecs_plain"].append(st.matvecs)
-            out["mismatch_plain"].append(st.mismatch_rel)
-            out["grad_rel_plain"].append(st.grad_rel)
-        torch.cuda.synchronize()
-        out["t_plain"] += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        v0s = [v.clone() for v in _predict_batch(model, chunk, n)]
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        _, stats = C.solve_batch(comb, v0s)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        out["t_predict"] += t1 - t0
-        out["t_solve_batch"] += t2 - t1
-        out["t_combined"] += t2 - t0
+            _, g0 = cp.objective_gradient(zeros())
+            gnorm0s.append(float(g0.abs().max()))
+            cp.set_options(gnorm0=gnorm0s[-1])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = cp.solve(zeros())
+            torch.cuda.synchronize()
+            t_plain += time.perf_counter() - t0
+        res["matvecs_plain"].append(st.matvecs)
+        res["mismatch_plain"].append(st.mismatch_rel)
+        res["grad_rel_plain"].append(st.grad_rel)
+    # combined arm: every context first (outside the timing), then the pipeline
+    comb = []
+    for (m0, m1), gn in zip(pairs, gnorm0s):
+        cc = C.Context((n, n, n), precision=1, graphs=1, warm_check=1, gnorm0=gn, **opts)
+        cc.set_images(m0, m1)
+        comb.append(cc)
+    chunks = [list(range(k, min(k + batch, len(pairs)))) for k in range(0, len(pairs), batch)]
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+
+    def predict(idx):
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            v0s = [v.clone() for v in _predict_batch(model, [pairs[i] for i in idx], n)]
+            ev = side.record_event()
+        return v0s, ev
+
+    fallbacks = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nxt = predict(chunks[0])
+    for k, idx in enumerate(chunks):
+        v0s, ev = nxt
+        main.wait_event(ev)
+        if k + 1 < len(chunks):
+            nxt = predict(chunks[k + 1])           # overlaps the solves of this chunk
+        _, stats = C.solve_batch([comb[i] for i in idx], v0s)
         for st in stats:
-            out["matvecs_combined"].append(st.matvecs)
-            out["mismatch_combined"].append(st.mismatch_rel)
-            out["grad_rel_combined"].append(st.grad_rel)
-            out["fallbacks"] += st.warm_fallback
-        for c in plain + comb:
-            c.close()
+            res["matvecs_combined"].append(st.matvecs)
+            res["mismatch_combined"].append(st.mismatch_rel)
+            res["grad_rel_combined"].append(st.grad_rel)
+            fallbacks += st.warm_fallback
+    torch.cuda.synchronize()
+    t_comb = time.perf_counter() - t0
+    for c in comb:
+        c.close()
     npairs = len(pairs)
-    summ = {"pairs": npairs, "batch": batch,
-            "t_plain_per_pair": out["t_plain"] / npairs,
-            "t_combined_per_pair": out["t_combined"] / npairs,
-            "t_predict_per_pair": out["t_predict"] / npairs,
-            "t_solve_batch_per_pair": out["t_solve_batch"] / npairs,
-            "speedup": out["t_plain"] / out["t_combined"], "fallbacks": out["fallbacks"]}
+    summ = {"pairs": npairs, "batch": batch, "t_plain_per_pair": t_plain / npairs,
+            "t_combined_per_pair": t_comb / npairs, "speedup": t_plain / t_comb,
+            "fallbacks": fallbacks}
     for k in ("matvecs", "mismatch", "grad_rel"):
         for arm in ("plain", "combined"):
-            summ[f"mean_{k}_{arm}"] = float(np.mean(out[f"{k}_{arm}"]))
-    summ["max_grad_rel"] = float(max(out["grad_rel_plain"] + out["grad_rel_combined"]))
+            summ[f"mean_{k}_{arm}"] = float(np.mean(res[f"{k}_{arm}"]))
+    summ["max_grad_rel"] = float(max(res["grad_rel_plain"] + res["grad_rel_combined"]))
     return summ
 
 
@@ -481,9 +492,9 @@ def main():
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--precond", type=int, default=PRECOND,
                     help="registration preconditioner: 0 spectral, 1 two-level")
-    ap.add_argument("--combined-batch", type=int, default=16,
-                    help="pairs per concurrent batch in the plain-vs-combined comparison "
-                         "(0 skips it)")
+    ap.add_argument("--combined-batch", default="16",
+                    help="comma-separated pairs per concurrent batch of the plain-vs-combined "
+                         "comparison (0 skips it)")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     globals()["PRECOND"] = args.precond
@@ -528,10 +539,12 @@ def main():
     summary["speedup_time"] = summary["mean_t_zero"] / summary["mean_t_warm"]
     summary["speedup_matvecs"] = summary["mean_matvecs_zero"] / max(1e-9, summary["mean_matvecs_warm"])
     log(json.dumps(summary))
-    if args.combined_batch > 0:
-        summary["combined"] = evaluate_combined(model, make_pairs(eval_seeds, n), n, args.beta,
-                                                batch=args.combined_batch)
-        log("plain vs combined: " + json.dumps(summary["combined"]))
+    summary["combined"] = []
+    for b in (int(x) for x in args.combined_batch.split(",")):
+        if b > 0:
+            summary["combined"].append(evaluate_combined(model, make_pairs(eval_seeds, n), n,
+                                                         args.beta, batch=b))
+            log("plain vs combined: " + json.dumps(summary["combined"][-1]))
     if args.out:
         with open(args.out, "w") as f:
             json.dump({"summary": summary, "pairs": res}, f, indent=1)

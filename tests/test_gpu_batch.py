@@ -81,6 +81,28 @@ def test_graph_replayed_pcg_equals_launch_by_launch(claire, precision):
     assert np.array_equal(out[0][0], out[1][0])
 
 
+@pytest.mark.parametrize("precision,inner", [(0, {}), (1, {}), (0, dict(max_inner=3)),
+                                              (0, dict(inner_rtol=1e-4, max_inner=40))])
+def test_graph_nested_cg_equals_host_loop(claire, precision, inner):
+    """With the two-level preconditioner a captured PCG part B holds the nested CG
+    as a conditional while node driven on the device: same iterates (bitwise), same
+    outer and nested iteration counts as the host-driven loop, also when the
+    iteration cap or a fixed tolerance ends the nested solves."""
+    shape = (48, 32, 40)
+    m0, m1, _ = synth.blob_pair(shape, seed=9, kmax=3, max_disp_voxels=2.5)
+    out = []
+    for graphs in (0, 1):
+        with claire.Context(shape, nt=4, beta_v=1e-3, graphs=graphs, precision=precision,
+                            precond=1, **inner) as ctx:
+            ctx.set_images(dev(m0), dev(m1))
+            v, st = ctx.solve_continuation([1e-1, 1e-2, 1e-3])
+            torch.cuda.synchronize()
+            out.append((v.cpu().numpy(), st.matvecs, st.pcg_iters, st.inner_iters))
+    assert out[0][3] > 0 and out[0][2] > 1
+    assert out[0][1:] == out[1][1:]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
 def test_autotuner_picks_valid_shapes_and_keeps_results(claire):
     shape = SHAPES[2]
     m0, m1, _ = synth.blob_pair(shape, seed=8, kmax=3, max_disp_voxels=2.0)
