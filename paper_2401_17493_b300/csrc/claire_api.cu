@@ -72,9 +72,9 @@ struct claire_ctx {
   // captured PCG iteration parts (options.graphs), indexed by
   // 4 * (departure-point buffer) + 2 * part + slot parity: the line search swaps
   // the two departure-point buffers, and kernel arguments are fixed at capture
-  cudaGraphExec_t graph_exec[8] = {};
-  long long graph_launches[8][K_COUNT] = {};
-  double graph_bytes[8][K_COUNT] = {};
+  cudaGraphExec_t graph_exec[9] = {};          // [8]: the PCG start (part S)
+  long long graph_launches[9][K_COUNT] = {};
+  double graph_bytes[9][K_COUNT] = {};
   float* dbuf0 = nullptr;       // first of the two departure-point buffers
   // two-level preconditioner (options.precond = 1), allocated on first use
   Grid gc{};                    // coarse grid, n_i / 2 points per axis
@@ -907,22 +907,29 @@ void drop_graphs(claire_ctx* c) {
     }
 }
 
-// Run part A (which = 0) or B (which = 1) for parity p, as a captured CUDA
-// graph when options.graphs is set (captured on first use; the kernels inside
-// are counted per replay, not event-timed).
+claire_status pcg_start(claire_ctx* c);
+
+// Run part A (which = 0) or B (which = 1) for parity p, or the PCG start S
+// (which = 2), as a captured CUDA graph when options.graphs is set (captured on
+// first use; the kernels inside are counted per replay, not event-timed).
 claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
-  // with the two-level preconditioner part B holds the nested CG as a conditional
-  // while node; if that capture is refused, part B runs launch by launch
-  if (!c->opt.graphs || (which == 1 && two_level(c) && c->tl_nograph))
-    return which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
-  const int slot = 4 * (c->df == c->dbuf0 ? 0 : 1) + 2 * which + (cur == SLOT_RZ0 ? 0 : 1);
+  // with the two-level preconditioner parts S and B hold the nested CG as a
+  // conditional while node; if that capture is refused, they run launch by launch
+  auto run = [&]() {
+    return which == 0 ? pcg_part_a(c, cur) : which == 1 ? pcg_part_b(c, cur, nxt)
+                                                        : pcg_start(c);
+  };
+  if (!c->opt.graphs || (which != 0 && two_level(c) && c->tl_nograph)) return run();
+  const int slot = which == 2 ? 8
+                              : 4 * (c->df == c->dbuf0 ? 0 : 1) + 2 * which +
+                                    (cur == SLOT_RZ0 ? 0 : 1);
   if (!c->graph_exec[slot]) {
     Profiler* saved = tl_prof;
     Profiler counter;                               // counts the captured launches
     tl_prof = &counter;
     cudaGraph_t graph = nullptr;
     CUDA_TRY(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-    claire_status s = which == 0 ? pcg_part_a(c, cur) : pcg_part_b(c, cur, nxt);
+    claire_status s = run();
     cudaError_t e = cudaStreamEndCapture(c->st, &graph);
     tl_prof = saved;
     if (s == CLAIRE_OK && e == cudaSuccess) {
@@ -930,7 +937,7 @@ claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
       if (e != cudaSuccess) c->graph_exec[slot] = nullptr;
     }
     if (graph) cudaGraphDestroy(graph);
-    if (which == 1 && two_level(c) && (s != CLAIRE_OK || e != cudaSuccess)) {
+    if (which != 0 && two_level(c) && (s != CLAIRE_OK || e != cudaSuccess)) {
       // nothing of the failed capture ran: run this part (and later ones) uncaptured
       cudaGetLastError();
       if (c->opt.verbose)
@@ -938,7 +945,7 @@ claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
                 c->err.empty() ? cudaGetErrorString(e) : c->err.c_str());
       c->err.clear();
       c->tl_nograph = true;
-      return pcg_part_b(c, cur, nxt);
+      return run();
     }
     if (s != CLAIRE_OK) return s;
     if (e != cudaSuccess) return fail(c, CLAIRE_ECUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -962,13 +969,28 @@ claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
 // so each iteration costs one FFT pair (the preconditioner) besides the
 // transport solves.  One host synchronisation per iteration reads <s, H s> and
 // ||r||^2 for the curvature and stopping tests.
+// Part S, the start of PCG: vt = 0, r = -g, z = M^-1 r with <r, z>, s = z and
+// beta_v L s (and ||s||_inf in mixed precision).
+claire_status pcg_start(claire_ctx* c) {
+  const int64_t N = N_of(c);
+  const int64_t n3 = 3 * N;
+  CUDA_TRY(c, cudaMemsetAsync(c->vt, 0, n3 * sizeof(float), c->st));
+  CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
+  CUDA_TRY(c, cudaMemsetAsync(c->slots + SLOT_TL_ITS, 0, sizeof(double), c->st));
+  launch_lincomb(n3, -1.0f, c->grad, 0.0f, c->grad, c->r, c->st);    // r = -g
+  TRY(precondition(c, SLOT_RZ0));
+  launch_s_update(N, c->slots + SLOT_RZ0, c->slots + SLOT_RZ0, lz_means(c), 1, c->z,
+                  lz_source(c), c->s, c->hs, c->st);
+  if (mixed(c))
+    launch_reduce(n3, c->s, nullptr, RED_ABSMAX, c->partial, c->red_blocks,
+                  c->slots + SLOT_VMAX, c->st);
+  return check_launch(c, "pcg start");
+}
+
 claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
   const int64_t N = N_of(c);
   const int64_t n3 = 3 * N;
   *curv = CLAIRE_OK;
-  CUDA_TRY(c, cudaMemsetAsync(c->vt, 0, n3 * sizeof(float), c->st));
-  CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
-  CUDA_TRY(c, cudaMemsetAsync(c->slots + SLOT_TL_ITS, 0, sizeof(double), c->st));
   // nested CG iterations run by captured part-B graphs (a running total on the
   // device): read with the slots after each part A, as every part B is followed
   // by one, and counted with their launches
@@ -983,14 +1005,8 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
         tl_prof->bytes[kk] += its * c->tl_body_bytes[kk];
       }
   };
-  launch_lincomb(n3, -1.0f, c->grad, 0.0f, c->grad, c->r, c->st);    // r = -g
   int cur = SLOT_RZ0;
-  TRY(precondition(c, cur));
-  launch_s_update(N, c->slots + cur, c->slots + cur, lz_means(c), 1, c->z, lz_source(c), c->s,
-                  c->hs, c->st);
-  if (mixed(c))
-    launch_reduce(n3, c->s, nullptr, RED_ABSMAX, c->partial, c->red_blocks,
-                  c->slots + SLOT_VMAX, c->st);
+  TRY(pcg_part(c, 2, cur, cur));
   for (int it = 1; it <= c->opt.max_pcg; ++it) {
     const int nxt = cur == SLOT_RZ0 ? SLOT_RZ1 : SLOT_RZ0;
     TRY(pcg_part(c, 0, cur, nxt));
@@ -1441,7 +1457,14 @@ claire_status claire_set_options(claire_ctx* c, const claire_options* o) {
     c->ph0 = h + 4 * (c->nt + 1) * N;
     c->ph1 = c->ph0 + N;
   }
-  drop_graphs(c);
+  // captured graphs bake the launch configuration, the stream and the kernel
+  // arguments; options read only on the host (tolerances, caps of the outer
+  // loops, gnorm0, warm_check, verbose) leave them valid
+  const claire_options& a = c->opt;
+  if (o->precision != a.precision || o->hessian != a.hessian || o->beta_w != a.beta_w ||
+      o->graphs != a.graphs || o->precond != a.precond || o->max_inner != a.max_inner ||
+      o->distance != a.distance || o->stream != a.stream || o->autotune != a.autotune)
+    drop_graphs(c);
   c->opt = *o;
   c->user = (cudaStream_t)o->stream;
   if (o->graphs && c->own == nullptr)
@@ -1820,6 +1843,7 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
       c->st = c->own;
       CUFFT_TRY(c, cufftSetStream(c->r2c, c->st));
       CUFFT_TRY(c, cufftSetStream(c->c2r, c->st));
+      TRY(tl_set_streams(c));                      // the two-level plans follow
     }
   }
   std::vector<claire_status> res(npairs, CLAIRE_OK);
@@ -1846,6 +1870,7 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
       c->st = saved[i];
       cufftSetStream(c->r2c, c->st);
       cufftSetStream(c->c2r, c->st);
+      if (tl_set_streams(c) != CLAIRE_OK && res[i] == CLAIRE_OK) res[i] = CLAIRE_ECUDA;
     }
   }
   claire_status worst = CLAIRE_OK;
@@ -1862,6 +1887,7 @@ claire_status claire_autotune(claire_ctx* c, int* sl_t1, int* march_t1) {
   ENTER(c);
   if (!c->have_eval) TRY(evaluate(c));
   TRY(autotune(c));
+  drop_graphs(c);                                  // captured with the previous shapes
   if (sl_t1) *sl_t1 = c->tune.sl_t1;
   if (march_t1) *march_t1 = c->tune.march_t1;
   return CLAIRE_OK;

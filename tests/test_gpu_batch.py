@@ -103,6 +103,26 @@ def test_graph_nested_cg_equals_host_loop(claire, precision, inner):
     assert np.array_equal(out[0][0], out[1][0])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reused_context_equals_fresh_context(claire, precision):
+    """A context reused for another pair (set_images, a new gnorm0, the captured graphs
+    kept) gives bitwise the registration of a fresh context."""
+    shape = (32, 32, 32)
+    pairs = [synth.blob_pair(shape, seed=s, kmax=3, max_disp_voxels=2.0)[:2] for s in (21, 22)]
+    opts = dict(nt=4, beta_v=1e-2, graphs=1, precision=precision, precond=1)
+    with claire.Context(shape, **opts) as ctx:
+        ctx.set_images(dev(pairs[0][0]), dev(pairs[0][1]))
+        ctx.solve()
+        ctx.set_images(dev(pairs[1][0]), dev(pairs[1][1]))
+        ctx.set_options(gnorm0=0.5)
+        v_reused, st_reused = ctx.solve()
+    with claire.Context(shape, gnorm0=0.5, **opts) as ctx:
+        ctx.set_images(dev(pairs[1][0]), dev(pairs[1][1]))
+        v_fresh, st_fresh = ctx.solve()
+    assert st_reused.matvecs == st_fresh.matvecs and st_reused.inner_iters == st_fresh.inner_iters
+    assert torch.equal(v_reused, v_fresh)
+
+
 def test_autotuner_picks_valid_shapes_and_keeps_results(claire):
     shape = SHAPES[2]
     m0, m1, _ = synth.blob_pair(shape, seed=8, kmax=3, max_disp_voxels=2.0)
