@@ -353,6 +353,8 @@ typedef struct {
   long long timed;      /* launches with an event-timed duration                     */
   double bytes;         /* algorithmic bytes of those launches                       */
   double ms;            /* summed event-timed duration                               */
+  double timed_bytes;   /* algorithmic bytes of the event-timed launches (launches inside
+                           captured graphs are counted but not timed)                */
 } claire_kernel_stat;
 
 /* Zero the counters; timing != 0 turns per-launch event timing on. */

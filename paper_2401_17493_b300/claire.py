@@ -62,7 +62,7 @@ class Stats(ctypes.Structure):
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong),
                 ("timed", ctypes.c_longlong), ("bytes", ctypes.c_double),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("timed_bytes", ctypes.c_double)]
 
 
 class ClaireError(RuntimeError):
@@ -407,12 +407,14 @@ class Context:
         self._check(self.lib.claire_profile_reset(self.h, 1 if timing else 0))
 
     def profile_read(self):
-        """{kernel class: dict(launches, timed, bytes, ms)} since the last reset."""
+        """{kernel class: dict(launches, timed, bytes, ms, timed_bytes)} since the last reset
+        (launches inside captured graphs are counted in launches and bytes, not timed)."""
         n = self.lib.claire_profile_read(self.h, None, 0)
         arr = (KernelStat * n)()
         got = self.lib.claire_profile_read(self.h, arr, n)
         if got < 0:
             raise ClaireError(ECUDA, "claire_profile_read failed")
         return {arr[i].name.decode(): {"launches": arr[i].launches, "timed": arr[i].timed,
-                                        "bytes": arr[i].bytes, "ms": arr[i].ms}
+                                        "bytes": arr[i].bytes, "ms": arr[i].ms,
+                                        "timed_bytes": arr[i].timed_bytes}
                 for i in range(got)}

@@ -1911,6 +1911,7 @@ int claire_profile_read(claire_ctx* c, claire_kernel_stat* out, int max) {
     out[n].timed = c->prof.timed[k];
     out[n].bytes = c->prof.bytes[k];
     out[n].ms = c->prof.ms[k];
+    out[n].timed_bytes = c->prof.timed_bytes[k];
   }
   return out ? n : (int)K_COUNT;
 }

@@ -55,6 +55,20 @@ __device__ __forceinline__ void cp_async_wait_prev() {      // all but the newes
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
+// Two FD8 first derivatives at once on packed FP32 pairs (fma.rn.f32x2): the same
+// arithmetic as fd8() per component, the differences as fused multiply-adds by -1.
+__device__ __forceinline__ float2 fd8_pair(float2 m4, float2 m3, float2 m2, float2 m1, float2 p1,
+                                           float2 p2, float2 p3, float2 p4, float2 inv_h) {
+  const float2 neg = make_float2(-1.0f, -1.0f);
+  const float c1 = 672.0f / 840.0f, c2 = 168.0f / 840.0f, c3 = 32.0f / 840.0f,
+              c4 = 3.0f / 840.0f;
+  float2 r = __fmul2_rn(make_float2(c1, c1), __ffma2_rn(neg, m1, p1));
+  r = __ffma2_rn(make_float2(-c2, -c2), __ffma2_rn(neg, m2, p2), r);
+  r = __ffma2_rn(make_float2(c3, c3), __ffma2_rn(neg, m3, p3), r);
+  r = __ffma2_rn(make_float2(-c4, -c4), __ffma2_rn(neg, m4, p4), r);
+  return __fmul2_rn(r, inv_h);
+}
+
 // Staging of plane i1 (tile plus the 4-node halo in x2 and x3) in chunks of 4
 // elements (16 bytes FP32, 8 bytes FP16).  The staged x3 window starts on a
 // multiple of 4, so with n3 % 4 == 0 a chunk never straddles the periodic
@@ -227,7 +241,8 @@ k_hist_march(Grid g, const T* __restrict__ mhist, const T* __restrict__ lhist,
     __syncthreads();                                           // plane i1 staged by all
     if (active) {
       const int64_t idx = (int64_t)i1 * s1 + col;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      float a0 = 0.f;
+      float2 a12 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const float* p;
@@ -235,24 +250,26 @@ k_hist_march(Grid g, const T* __restrict__ mhist, const T* __restrict__ lhist,
         else p = sp[cur][f];
         const float gx = fd8(q[f][0], q[f][1], q[f][2], q[f][3], q[f][5], q[f][6], q[f][7],
                              q[f][8], g.inv_h1);
-        const float gy = fd8(p[c - 4 * MP3], p[c - 3 * MP3], p[c - 2 * MP3], p[c - MP3],
-                             p[c + MP3], p[c + 2 * MP3], p[c + 3 * MP3], p[c + 4 * MP3],
-                             g.inv_h2);
-        const float gz = fd8(p[c - 4], p[c - 3], p[c - 2], p[c - 1], p[c + 1], p[c + 2],
-                             p[c + 3], p[c + 4], g.inv_h3);
+        // the x2 and x3 derivatives as one packed FP32 pair
+        const float2 gyz = fd8_pair(
+            make_float2(p[c - 4 * MP3], p[c - 4]), make_float2(p[c - 3 * MP3], p[c - 3]),
+            make_float2(p[c - 2 * MP3], p[c - 2]), make_float2(p[c - MP3], p[c - 1]),
+            make_float2(p[c + MP3], p[c + 1]), make_float2(p[c + 2 * MP3], p[c + 2]),
+            make_float2(p[c + 3 * MP3], p[c + 3]), make_float2(p[c + 4 * MP3], p[c + 4]),
+            make_float2(g.inv_h2, g.inv_h3));
         if (MODE == 0) {
           float sd = gx * (sig * xc[0]);
-          sd = fmaf(gy, sig * xc[1], sd);
-          sd = fmaf(gz, sig * xc[2], sd);
+          sd = fmaf(gyz.x, sig * xc[1], sd);
+          sd = fmaf(gyz.y, sig * xc[2], sd);
           hout[f * N + idx] = from_f<T>(f == 0 ? scale0 * sd : sd);
         } else {
           const float wl = (f == 0 || f == nt) ? 0.5f * lc[f] : lc[f];
           a0 = fmaf(wl, gx, a0);
-          a1 = fmaf(wl, gy, a1);
-          a2 = fmaf(wl, gz, a2);
+          a12 = __ffma2_rn(make_float2(wl, wl), gyz, a12);
         }
       }
       if (MODE == 1) {
+        float a1 = a12.x, a2 = a12.y;
         a0 *= unscale; a1 *= unscale; a2 *= unscale;
         if (has_base) {
           a0 = fmaf(base_coef, xc[0], a0);

@@ -28,7 +28,8 @@ struct Profiler {
   double bytes[K_COUNT] = {};
   double ms[K_COUNT] = {};
   long long timed[K_COUNT] = {};
-  struct Pending { int kind; cudaEvent_t a, b; };
+  double timed_bytes[K_COUNT] = {};   // algorithmic bytes of the event-timed launches
+  struct Pending { int kind; cudaEvent_t a, b; double bytes; };
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
   void reset(bool timing_on);
@@ -53,6 +54,7 @@ int tuned_march_t1();
 
 struct ProfileRange {
   int kind;
+  double bytes;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   ProfileRange(int k, double bytes, cudaStream_t s);

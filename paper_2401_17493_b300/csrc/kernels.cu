@@ -629,6 +629,7 @@ void Profiler::reset(bool timing_on) {
     bytes[k] = 0.0;
     ms[k] = 0.0;
     timed[k] = 0;
+    timed_bytes[k] = 0.0;
   }
 }
 
@@ -652,6 +653,7 @@ cudaError_t Profiler::resolve() {
     if (e == cudaSuccess) {
       ms[p.kind] += t;
       timed[p.kind] += 1;
+      timed_bytes[p.kind] += p.bytes;
     } else if (err == cudaSuccess) {
       err = e;
     }
@@ -668,7 +670,7 @@ void Profiler::release() {
   pool.clear();
 }
 
-ProfileRange::ProfileRange(int k, double b, cudaStream_t s) : kind(k), st(s) {
+ProfileRange::ProfileRange(int k, double b, cudaStream_t s) : kind(k), bytes(b), st(s) {
   Profiler* p = tl_prof;
   if (!p) return;
   p->launches[k] += 1;
@@ -685,7 +687,7 @@ ProfileRange::~ProfileRange() {
   cudaEvent_t b = p->take();
   if (!b) return;
   cudaEventRecord(b, st);
-  p->pending.push_back({kind, a, b});
+  p->pending.push_back({kind, a, b, bytes});
   if (p->pending.size() > 8192) p->resolve();
 }
 

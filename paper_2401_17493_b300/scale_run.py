@@ -66,7 +66,7 @@ def main():
     except Exception:
         peak = 6400.0
     kern = {k: {"launches": p["launches"], "ms": p["ms"],
-                "gbs": p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else None}
+                "gbs": p["timed_bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else None}
             for k, p in prof.items() if p["launches"]}
     sl = kern.get("sl_step", {})
     res = {

@@ -379,9 +379,13 @@ def evaluate(model, pairs, n, beta, eps_opt=5e-2):
                        max_inner=MAX_INNER) as ctx:
             ctx.set_images(m0, m1)
             z = torch.zeros((3, n, n, n), device="cuda")
-            # |g(0)| is shared by both arms (the same stopping test)
+            # |g(0)| is shared by both arms (the same stopping test); the relative
+            # gradient at the prediction is a diagnostic (outside the timings)
             _, g0 = ctx.objective_gradient(z)
-            ctx.set_options(gnorm0=float(g0.abs().max()))
+            gnorm0 = float(g0.abs().max())
+            ctx.set_options(gnorm0=gnorm0)
+            _, gp = ctx.objective_gradient(v0)
+            grad_rel_pred = float(gp.abs().max()) / gnorm0
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             vz, sz = ctx.solve(torch.zeros_like(z))
@@ -396,7 +400,8 @@ def evaluate(model, pairs, n, beta, eps_opt=5e-2):
                     "matvecs_warm": sw.matvecs, "newton_zero": sz.newton_iters,
                     "newton_warm": sw.newton_iters, "grad_rel_zero": sz.grad_rel,
                     "grad_rel_warm": sw.grad_rel, "mismatch_zero": sz.mismatch_rel,
-                    "mismatch_warm": sw.mismatch_rel, "fallback": bool(sw.warm_fallback)})
+                    "mismatch_warm": sw.mismatch_rel, "fallback": bool(sw.warm_fallback),
+                    "grad_rel_pred": grad_rel_pred})
     return res
 
 
@@ -545,6 +550,8 @@ def main():
         "mean_mismatch_zero": float(np.mean([r["mismatch_zero"] for r in res])),
         "mean_mismatch_warm": float(np.mean([r["mismatch_warm"] for r in res])),
         "fallbacks": int(sum(r["fallback"] for r in res)),
+        "median_grad_rel_pred": float(np.median([r["grad_rel_pred"] for r in res])),
+        "frac_pred_within_tol": float(np.mean([r["grad_rel_pred"] <= 5e-2 for r in res])),
         "all_converged": bool(all(r["grad_rel_zero"] <= 5e-2 and r["grad_rel_warm"] <= 5e-2
                                   for r in res)),
     }
