@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-pair batched workload")
     ap.add_argument("--batch-pairs", type=int, default=32)
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay the PCG parts of the 256^3 solves as CUDA graphs (default); 0 "
+                         "launches every kernel (profilers list the kernels inside graphs that "
+                         "hold a conditional node only this way)")
     return ap.parse_args()
 
 
@@ -275,7 +279,8 @@ def run_claire(args, world, rank, local):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     m0d, m1d = dev(m0), dev(m1)
     ctx = claire.Context(shape, nt=NT, beta_v=BETAS[0], eps_opt=EPS_OPT, max_newton=50,
-                         max_pcg=MAX_PCG, precond=PRECOND, max_inner=MAX_INNER, graphs=1)
+                         max_pcg=MAX_PCG, precond=PRECOND, max_inner=MAX_INNER,
+                         graphs=args.graphs)
     ctx.set_images(m0d, m1d)
     stream = torch.cuda.current_stream()
     v = torch.zeros((3,) + shape, device="cuda")
@@ -439,8 +444,8 @@ def run_claire(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": f"{n}^3 ellipsoid phantom pair (seed {SEED}), beta_v continuation "
                                "1e-1..1e-4, rel-grad 5e-2 per level, nt 4, H1 seminorm, FP32, "
-                               "two-level zero-velocity preconditioner, PCG parts replayed "
-                               "as CUDA graphs",
+                               "two-level zero-velocity preconditioner" +
+                               (", PCG parts replayed as CUDA graphs" if args.graphs else ""),
                    "l2": "working set ~%.1f GB > 126 MB L2" % (ctx.workspace_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "matvecs_per_s": matvecs_per_s,
