@@ -81,6 +81,25 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_max(x):
+    """Max of a float over the ranks of the initialised process group (the timed
+    region of the slowest replica); the value itself in a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_registration(t_max, steps, world):
+    """Whole-job time per registration: `world` replicas each registered `steps`
+    pairs within the slowest replica's time t_max (any unit)."""
+    return t_max / (steps * world)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
 
@@ -312,12 +331,8 @@ def run_claire(args, world, rank, local):
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
     prof = ctx.profile_read()
-    t_max = ms_total
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    s_per_solve = t_max / 1e3 / (args.steps * world)
+    t_max = reduce_max(ms_total)
+    s_per_solve = per_registration(t_max / 1e3, args.steps, world)
     launches_per_step = sum(p["launches"] for k, p in prof.items() if k != "cufft") / args.steps
 
     # the same solve with the spectral preconditioner (beta_v L)^-1
@@ -408,11 +423,7 @@ def run_claire(args, world, rank, local):
         t0 = time.perf_counter()
         ctx.solve_host(m0h, m1h, vh, BETAS)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_times))
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item()) / world
+    e2e_s = per_registration(reduce_max(sum(e2e_times)), len(e2e_times), world)
 
     peak, peak_src = peaks()
     mine = {k: p for k, p in prof.items() if k != "cufft" and p["timed"] > 0}

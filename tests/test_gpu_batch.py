@@ -103,6 +103,30 @@ def test_graph_nested_cg_equals_host_loop(claire, precision, inner):
     assert np.array_equal(out[0][0], out[1][0])
 
 
+def test_graph_replays_are_counted_like_launches(claire):
+    """The launch accounting of a solve is the same with and without graphs: captured
+    parts count their kernels per replay, the nested CG's while-node body per device
+    iteration (read back with the PCG scalars).  The preconditioner class differs by
+    design: the device loop adds its begin and control kernels and updates the
+    direction after the last iteration too."""
+    shape = (32, 32, 32)
+    m0, m1, _ = synth.blob_pair(shape, seed=23, kmax=3, max_disp_voxels=2.0)
+    counts = []
+    for graphs in (0, 1):
+        with claire.Context(shape, nt=4, beta_v=1e-3, graphs=graphs, precond=1) as ctx:
+            ctx.set_images(dev(m0), dev(m1))
+            ctx.solve()                                # captures the graphs
+            ctx.profile_reset(timing=False)
+            _, st = ctx.solve()
+            prof = ctx.profile_read()
+        counts.append({k: (p["launches"], round(p["bytes"])) for k, p in prof.items()})
+        assert st.inner_iters > 0
+    host, graph = counts
+    assert graph["precond"][0] > host["precond"][0] > 0
+    del host["precond"], graph["precond"]
+    assert host == graph
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_reused_context_equals_fresh_context(claire, precision):
     """A context reused for another pair (set_images, a new gnorm0, the captured graphs
