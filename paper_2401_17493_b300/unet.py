@@ -14,7 +14,7 @@ flip_weights, claire_unet_op / bias_grad / pack / mse / adam,
 claire_resample); this module only sequences them and owns the buffers
 (torch CUDA tensors).
 
-    python -m paper_2401_17493_b300.unet --train 2000 --eval 200 --epochs 8 --out results.json
+    python -m paper_2401_17493_b300.unet --train 2000 --eval 200 --epochs 40 --out results.json
 """
 
 import argparse
@@ -391,6 +391,12 @@ def evaluate(model, pairs, n, beta, eps_opt=5e-2):
             vz, sz = ctx.solve(torch.zeros_like(z))
             torch.cuda.synchronize()
             tz = time.perf_counter() - t0
+            # the representation floor (diagnostic): the zero-init solution restricted to
+            # 64^3 and prolonged back, as the network's output is
+            vr = resample(resample(vz.contiguous(), (n, n, n), (64, 64, 64), 3).contiguous(),
+                          (64, 64, 64), (n, n, n), 3).contiguous()
+            _, gr = ctx.objective_gradient(vr)
+            grad_rel_floor = float(gr.abs().max()) / gnorm0
             ctx.set_options(warm_check=1)
             t0 = time.perf_counter()
             vw, sw = ctx.solve(v0)
@@ -401,7 +407,7 @@ def evaluate(model, pairs, n, beta, eps_opt=5e-2):
                     "newton_warm": sw.newton_iters, "grad_rel_zero": sz.grad_rel,
                     "grad_rel_warm": sw.grad_rel, "mismatch_zero": sz.mismatch_rel,
                     "mismatch_warm": sw.mismatch_rel, "fallback": bool(sw.warm_fallback),
-                    "grad_rel_pred": grad_rel_pred})
+                    "grad_rel_pred": grad_rel_pred, "grad_rel_floor": grad_rel_floor})
     return res
 
 
@@ -504,7 +510,7 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--eval", type=int, default=200)
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--beta", type=float, default=1e-2)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--precond", type=int, default=PRECOND,
@@ -552,6 +558,7 @@ def main():
         "fallbacks": int(sum(r["fallback"] for r in res)),
         "median_grad_rel_pred": float(np.median([r["grad_rel_pred"] for r in res])),
         "frac_pred_within_tol": float(np.mean([r["grad_rel_pred"] <= 5e-2 for r in res])),
+        "median_grad_rel_floor": float(np.median([r["grad_rel_floor"] for r in res])),
         "all_converged": bool(all(r["grad_rel_zero"] <= 5e-2 and r["grad_rel_warm"] <= 5e-2
                                   for r in res)),
     }
