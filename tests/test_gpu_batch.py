@@ -103,6 +103,25 @@ def test_graph_nested_cg_equals_host_loop(claire, precision, inner):
     assert np.array_equal(out[0][0], out[1][0])
 
 
+@pytest.mark.parametrize("opts", [dict(distance=1), dict(hessian=1), dict(beta_w=1e-3),
+                                  dict(precision=1, precond=0)])
+def test_graph_replay_equals_launch_by_launch_in_every_mode(claire, opts):
+    """Graph replay is bitwise launch-by-launch execution also with the NCC distance,
+    full Newton, the near-incompressible term and mixed precision with the spectral
+    preconditioner."""
+    shape = (32, 32, 32)
+    m0, m1, _ = synth.blob_pair(shape, seed=27, kmax=3, max_disp_voxels=2.0)
+    out = []
+    for graphs in (0, 1):
+        with claire.Context(shape, nt=4, beta_v=1e-3, graphs=graphs, **opts) as ctx:
+            ctx.set_images(dev(m0), dev(m1))
+            v, st = ctx.solve_continuation([1e-2, 1e-3])
+            torch.cuda.synchronize()
+            out.append((v.cpu().numpy(), st.matvecs, st.pcg_iters, st.inner_iters, st.status))
+    assert out[0][1:] == out[1][1:]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
 def test_graph_replays_are_counted_like_launches(claire):
     """The launch accounting of a solve is the same with and without graphs: captured
     parts count their kernels per replay, the nested CG's while-node body per device
