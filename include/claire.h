@@ -105,8 +105,9 @@ claire_status claire_default_options(claire_options* opt);
 /* Create a context for an nx x ny x nz grid with nt time steps, regularisation
  * weight beta_v (alpha in Sec. 2.2) and operator exponent gamma
  * (L = (-Laplacian)^gamma, gamma = 1: H1 seminorm).  Sizes must be even and
- * >= 16, nt >= 1, beta_v > 0, gamma > 0, else EINVAL.  Allocates the whole
- * workspace (ENOMEM / ECUDA on failure, *out left NULL). */
+ * >= 16 with 3 nx ny nz < 2^31 (the largest cube is 894^3), nt >= 1,
+ * beta_v > 0, gamma > 0, else EINVAL.  Allocates the whole workspace
+ * (ENOMEM / ECUDA on failure, *out left NULL). */
 claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, double gamma,
                             claire_ctx** out);
 claire_status claire_set_options(claire_ctx* ctx, const claire_options* opt);

@@ -53,6 +53,9 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.claire_create(64, 8, 64, 4, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
     assert lib.claire_create(64, 64, 64, 0, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
     assert lib.claire_create(64, 64, 64, 4, 0.0, 1.0, ctypes.byref(h)) == claire.EINVAL
+    # largest grid: 3 N must fit the 32-bit element counts of the kernels (N < 2^31 / 3)
+    assert lib.claire_create(1024, 1024, 1024, 4, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
+    assert lib.claire_create(896, 896, 896, 4, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
     assert h.value is None
     assert lib.claire_destroy(None) == claire.OK
     assert lib.claire_last_error(None) == b"null context"
