@@ -84,6 +84,7 @@ struct claire_ctx {
   cufftComplex *tl_sx = nullptr, *tl_sr = nullptr, *tl_sp = nullptr, *tl_sap = nullptr;
   float *tl_gm = nullptr, *tl_mc = nullptr, *tl_q = nullptr, *tl_w = nullptr;
   float2* tl_fw = nullptr;      // per coarse mode: R^-1/2 symbol and Parseval weight
+  unsigned* tl_count = nullptr; // block ticket of the nested CG's last-block reductions (0)
   bool tl_ready = false, tl_image = false;
   double tl_rtol = 1e-3;        // nested CG relative tolerance of the current PCG
   int tl_iters = 0;             // nested CG iterations not yet counted in the stats
@@ -592,6 +593,11 @@ claire_status tl_setup(claire_ctx* c) {
     TRY(alloc(c, &p, 3 * Nh * 2));
     c->cbuf2 = (cufftComplex*)p;
   }
+  if (!c->tl_count) {
+    TRY(alloc(c, &p, 1));
+    c->tl_count = reinterpret_cast<unsigned*>(p);
+    CUDA_TRY(c, cudaMemsetAsync(c->tl_count, 0, sizeof(unsigned), c->st));
+  }
   int nc[3] = {gc.n1, gc.n2, gc.n3};
   if ((!c->tl_r2c1 && cufftPlan3d(&c->tl_r2c1, g.n1, g.n2, g.n3, CUFFT_R2C) != CUFFT_SUCCESS) ||
       (!c->tl_c2r1 && cufftPlan3d(&c->tl_c2r1, gc.n1, gc.n2, gc.n3, CUFFT_C2R) != CUFFT_SUCCESS) ||
@@ -699,7 +705,6 @@ claire_status tl_cg_graph(claire_ctx* c) {
   auto iteration = [&]() -> claire_status {
     CUFFT_TRY(c, cufftSetStream(c->tl_c2r3, bs));
     CUFFT_TRY(c, cufftSetStream(c->tl_r2c3, bs));
-    launch_tl_spec_scale(gc, c->tl_fw, c->tl_sp, c->tl_cc, 1.0f, bs);
     {
       ProfileRange pr(K_CUFFT, fft_c, bs);
       CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)c->tl_q));
@@ -710,11 +715,11 @@ claire_status tl_cg_graph(claire_ctx* c) {
       CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)c->tl_w, c->tl_cc));
     }
     launch_tl_spec_finish(gc, c->tl_fw, c->tl_sp, c->tl_cc, c->tl_sap, inv_nc, c->partial,
-                          sl + SLOT_TL_PAP, bs);
+                          c->tl_count, sl + SLOT_TL_PAP, bs);
     launch_tl_spec_step(gc, c->tl_fw, sl + SLOT_TL_RR0, sl + SLOT_TL_PAP, c->tl_sx, c->tl_sr,
-                        c->tl_sp, c->tl_sap, c->partial, sl + SLOT_TL_RR1, bs);
-    launch_tl_cg_dir(6 * Ch, sl + SLOT_TL_RR1, sl + SLOT_TL_RR0, (const float*)c->tl_sr,
-                     (float*)c->tl_sp, bs);
+                        c->tl_sp, c->tl_sap, c->partial, c->tl_count, sl + SLOT_TL_RR1, bs);
+    launch_tl_dir_scale(gc, c->tl_fw, sl + SLOT_TL_RR1, sl + SLOT_TL_RR0, c->tl_sr, c->tl_sp,
+                        c->tl_cc, bs);
     launch_tl_cg_control(h, sl + SLOT_TL_RR0, sl + SLOT_TL_RR1, sl + SLOT_TL_PAP,
                          sl + SLOT_TL_STOP, sl + SLOT_TL_COUNT, sl + SLOT_TL_ITS,
                          c->opt.max_inner, bs);
@@ -758,7 +763,7 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
   // read per iteration; two coarse FFTs per operator application
   int cur = SLOT_TL_RR0, nxt = SLOT_TL_RR1;
   launch_tl_spec_init(gc, c->tl_fw, c->tl_cc, c->tl_sx, c->tl_sr, c->tl_sp, c->partial,
-                      c->slots + cur, c->st);
+                      c->tl_count, c->slots + cur, c->st);
   TRY(check_launch(c, "nested cg"));
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CUDA_TRY(c, cudaStreamIsCapturing(c->st, &cs));
@@ -773,8 +778,8 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
   const float inv_nc = (float)(1.0 / (double)gc.N);
   int it = 0;
   while (it < c->opt.max_inner && rr > stop2 && std::isfinite(rr)) {
-    // A p = p + R^-1/2 (grad m_c (grad m_c . R^-1/2 p)) with R^-1/2 diagonal in k
-    launch_tl_spec_scale(gc, c->tl_fw, c->tl_sp, c->tl_cc, 1.0f, c->st);
+    // A p = p + R^-1/2 (grad m_c (grad m_c . R^-1/2 p)) with R^-1/2 diagonal in k;
+    // tl_cc holds R^-1/2 p (from the initialisation or the last direction update)
     {
       ProfileRange pr(K_CUFFT, fft_c, c->st);
       CUFFT_TRY(c, cufftExecC2R(c->tl_c2r3, c->tl_cc, (cufftReal*)c->tl_q));
@@ -785,9 +790,10 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
       CUFFT_TRY(c, cufftExecR2C(c->tl_r2c3, (cufftReal*)c->tl_w, c->tl_cc));
     }
     launch_tl_spec_finish(gc, c->tl_fw, c->tl_sp, c->tl_cc, c->tl_sap, inv_nc, c->partial,
-                          c->slots + SLOT_TL_PAP, c->st);
+                          c->tl_count, c->slots + SLOT_TL_PAP, c->st);
     launch_tl_spec_step(gc, c->tl_fw, c->slots + cur, c->slots + SLOT_TL_PAP, c->tl_sx,
-                        c->tl_sr, c->tl_sp, c->tl_sap, c->partial, c->slots + nxt, c->st);
+                        c->tl_sr, c->tl_sp, c->tl_sap, c->partial, c->tl_count, c->slots + nxt,
+                        c->st);
     TRY(check_launch(c, "nested cg"));
     CUDA_TRY(c, cudaMemcpyAsync(c->hres, c->slots + SLOT_TL_RR0, 3 * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->st));
@@ -797,8 +803,8 @@ claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz
     if (!(pAp > 0.0) || !std::isfinite(pAp)) break;   // x, r unchanged by this step
     rr = c->hres[nxt - SLOT_TL_RR0];
     if (rr <= stop2) break;
-    launch_tl_cg_dir(6 * Ch, c->slots + nxt, c->slots + cur, (const float*)c->tl_sr,
-                     (float*)c->tl_sp, c->st);
+    launch_tl_dir_scale(gc, c->tl_fw, c->slots + nxt, c->slots + cur, c->tl_sr, c->tl_sp,
+                        c->tl_cc, c->st);
     std::swap(cur, nxt);
   }
   c->tl_iters += it;

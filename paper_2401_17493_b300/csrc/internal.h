@@ -125,8 +125,6 @@ void launch_tl_split(const Grid& gf, cufftComplex* X, cufftComplex* C, int ncomp
 void launch_tl_merge(const Grid& gf, cufftComplex* X, const cufftComplex* C, cufftComplex* X2,
                      float alpha, float gamma, float sf, float sc, cudaStream_t st);
 void launch_tl_outer(int64_t n, const float* gm, const float* q, float* w, cudaStream_t st);
-void launch_tl_cg_dir(int64_t n, const double* rr_new, const double* rr_old, const float* r,
-                      float* p, cudaStream_t st);
 void launch_tl_unscale_h(int64_t n, const __half* h, float inv, float* out, cudaStream_t st);
 // Device-side control of the nested CG inside a graph with a conditional while node.
 void launch_tl_cg_begin(cudaGraphConditionalHandle h, const double* rr0, const double* rtol,
@@ -137,18 +135,22 @@ void launch_tl_cg_control(cudaGraphConditionalHandle h, double* rr, const double
 void launch_set_scalar(double* p, double v, cudaStream_t st);
 int tl_spec_blocks(const Grid& gc);
 void launch_tl_spec_table(const Grid& gc, float alpha, float gamma, float2* fw, cudaStream_t st);
-void launch_tl_spec_scale(const Grid& gc, const float2* fw, const cufftComplex* in,
-                          cufftComplex* out, float scale, cudaStream_t st);
+// Nested CG on coarse half spectra.  Each scalar (<b,b>, <p,Ap>, ||r||^2) is finished
+// by the last block of its kernel; count points to a zeroed counter the kernel
+// leaves at zero.
 void launch_tl_spec_finish(const Grid& gc, const float2* fw, const cufftComplex* p,
                            const cufftComplex* y, cufftComplex* Ap, float scale, double* partial,
-                           double* pAp, cudaStream_t st);
+                           unsigned* count, double* pAp, cudaStream_t st);
 void launch_tl_spec_step(const Grid& gc, const float2* fw, const double* rr, const double* pAp,
                          cufftComplex* x, cufftComplex* r, const cufftComplex* p,
-                         const cufftComplex* Ap, double* partial, double* rr_new,
-                         cudaStream_t st);
-void launch_tl_spec_init(const Grid& gc, const float2* fw, const cufftComplex* b, cufftComplex* x,
-                         cufftComplex* r, cufftComplex* p, double* partial, double* bb,
-                         cudaStream_t st);
+                         const cufftComplex* Ap, double* partial, unsigned* count,
+                         double* rr_new, cudaStream_t st);
+void launch_tl_spec_init(const Grid& gc, const float2* fw, cufftComplex* b, cufftComplex* x,
+                         cufftComplex* r, cufftComplex* p, double* partial, unsigned* count,
+                         double* bb, cudaStream_t st);
+void launch_tl_dir_scale(const Grid& gc, const float2* fw, const double* rr_new,
+                         const double* rr_old, const cufftComplex* r, cufftComplex* p,
+                         cufftComplex* cc, cudaStream_t st);
 
 enum ReduceMode {
   RED_DOT = 0, RED_SQDIFF = 1, RED_ABSMAX = 2, RED_SQ = 3, RED_MAX = 4, RED_MIN = 5, RED_SUM = 6

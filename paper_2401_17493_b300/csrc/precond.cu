@@ -112,16 +112,6 @@ __global__ void k_tl_outer(int64_t n, const float* __restrict__ gm, const float*
   }
 }
 
-// p = r + (rr_new / rr_old) p.
-__global__ void k_tl_cg_dir(int64_t n, const double* __restrict__ rr_new,
-                            const double* __restrict__ rr_old, const float* __restrict__ r,
-                            float* __restrict__ p) {
-  const float b = (float)(*rr_new / *rr_old);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fmaf(b, p[i], r[i]);
-}
-
 // ---- nested CG in the coarse spectral domain.  Vectors are coarse half spectra
 // [3][Ch] in the normalisation of cuFFT's unnormalised C2R (u = C2R(u^)), so the
 // split kernel's output is the right-hand side and the merge kernel reads the
@@ -152,33 +142,40 @@ __global__ void k_tl_spec_table(int64_t Ch, int n1, int n2, int n3, float alpha,
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < Ch;                \
        m += (int64_t)gridDim.x * blockDim.x)
 
-__device__ __forceinline__ void spec_partial(double* partial, const KahanF& acc) {
+// The block's share goes to partial[blockIdx.x]; the last block to finish (a ticket
+// on *count) adds the shares in block order, writes *out and resets *count, so a
+// CG scalar needs no separate final-reduction launch.  The shares are read past L1
+// after the fences, and the order of the final sum is fixed.
+__device__ __forceinline__ void spec_partial_final(double* partial, const KahanF& acc,
+                                                   unsigned* count, double* out) {
+  __shared__ bool last;
   const double b = block_sum(acc.value());
-  if (threadIdx.x == 0) partial[blockIdx.x] = b;
-}
-
-// out = scale R^-1/2 in.
-__global__ void k_tl_spec_scale(int64_t Ch, const float2* __restrict__ fw,
-                                const cufftComplex* __restrict__ in,
-                                cufftComplex* __restrict__ out, float scale) {
-  CLAIRE_SPEC_LOOP {
-    const float f = scale * fw[m].x;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const cufftComplex v = in[a * Ch + m];
-      out[a * Ch + m] = make_cuComplex(f * v.x, f * v.y);
-    }
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += __ldcg(partial + i);
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    *out = v;
+    *count = 0u;
   }
 }
 
-// Ap = p + scale R^-1/2 y (y = R2C of the pointwise product) and the block's
-// share of <p, Ap>.
+// Ap = p + scale R^-1/2 y (y = R2C of the pointwise product) and <p, Ap>.
 __global__ void __launch_bounds__(256) k_tl_spec_finish(int64_t Ch, const float2* __restrict__ fw,
                                                         const cufftComplex* __restrict__ p,
                                                         const cufftComplex* __restrict__ y,
                                                         cufftComplex* __restrict__ Ap,
                                                         float scale,
-                                                        double* __restrict__ partial) {
+                                                        double* __restrict__ partial,
+                                                        unsigned* __restrict__ count,
+                                                        double* __restrict__ pAp) {
   KahanF acc;
   CLAIRE_SPEC_LOOP {
     const float2 t = fw[m];
@@ -193,11 +190,11 @@ __global__ void __launch_bounds__(256) k_tl_spec_finish(int64_t Ch, const float2
     }
     acc.add(t.y * d);
   }
-  spec_partial(partial, acc);
+  spec_partial_final(partial, acc, count, pAp);
 }
 
 // CG step on spectra: a = rr / pAp (0 when pAp <= 0 or not finite), x += a p,
-// r -= a Ap, and the block's share of ||r||^2.
+// r -= a Ap, and ||r||^2 into *rr_new.
 __global__ void __launch_bounds__(256) k_tl_spec_step(int64_t Ch, const float2* __restrict__ fw,
                                                       const double* __restrict__ rr,
                                                       const double* __restrict__ pAp,
@@ -205,7 +202,9 @@ __global__ void __launch_bounds__(256) k_tl_spec_step(int64_t Ch, const float2* 
                                                       cufftComplex* __restrict__ r,
                                                       const cufftComplex* __restrict__ p,
                                                       const cufftComplex* __restrict__ Ap,
-                                                      double* __restrict__ partial) {
+                                                      double* __restrict__ partial,
+                                                      unsigned* __restrict__ count,
+                                                      double* __restrict__ rr_new) {
   const double q = *pAp;
   const float a = (q > 0.0 && isfinite(q)) ? (float)(*rr / q) : 0.0f;
   KahanF acc;
@@ -224,18 +223,22 @@ __global__ void __launch_bounds__(256) k_tl_spec_step(int64_t Ch, const float2* 
     }
     acc.add(fw[m].y * d);
   }
-  spec_partial(partial, acc);
+  spec_partial_final(partial, acc, count, rr_new);
 }
 
-// x = 0, r = p = b, and the block's share of ||b||^2.
+// x = 0, r = p = b, ||b||^2 into *bb, and b in place scaled to R^-1/2 b: the input
+// of the first operator application.
 __global__ void __launch_bounds__(256) k_tl_spec_init(int64_t Ch, const float2* __restrict__ fw,
-                                                      const cufftComplex* __restrict__ b,
+                                                      cufftComplex* __restrict__ b,
                                                       cufftComplex* __restrict__ x,
                                                       cufftComplex* __restrict__ r,
                                                       cufftComplex* __restrict__ p,
-                                                      double* __restrict__ partial) {
+                                                      double* __restrict__ partial,
+                                                      unsigned* __restrict__ count,
+                                                      double* __restrict__ bb) {
   KahanF acc;
   CLAIRE_SPEC_LOOP {
+    const float2 t = fw[m];
     float d = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -244,11 +247,33 @@ __global__ void __launch_bounds__(256) k_tl_spec_init(int64_t Ch, const float2* 
       x[i] = make_cuComplex(0.f, 0.f);
       r[i] = v;
       p[i] = v;
+      b[i] = make_cuComplex(t.x * v.x, t.x * v.y);
       d = fmaf(v.x, v.x, fmaf(v.y, v.y, d));
     }
-    acc.add(fw[m].y * d);
+    acc.add(t.y * d);
   }
-  spec_partial(partial, acc);
+  spec_partial_final(partial, acc, count, bb);
+}
+
+// p = r + (rr_new / rr_old) p, and R^-1/2 p into cc: the direction update fused
+// with the scaling that starts the next operator application.
+__global__ void k_tl_dir_scale(int64_t Ch, const float2* __restrict__ fw,
+                               const double* __restrict__ rr_new,
+                               const double* __restrict__ rr_old,
+                               const cufftComplex* __restrict__ r, cufftComplex* __restrict__ p,
+                               cufftComplex* __restrict__ cc) {
+  const float bt = (float)(*rr_new / *rr_old);
+  CLAIRE_SPEC_LOOP {
+    const float f = fw[m].x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t i = c * Ch + m;
+      const cufftComplex rv = r[i], pv = p[i];
+      const cufftComplex q = make_cuComplex(fmaf(bt, pv.x, rv.x), fmaf(bt, pv.y, rv.y));
+      p[i] = q;
+      cc[i] = make_cuComplex(f * q.x, f * q.y);
+    }
+  }
 }
 #undef CLAIRE_SPEC_LOOP
 
@@ -283,11 +308,6 @@ void launch_tl_outer(int64_t n, const float* gm, const float* q, float* w, cudaS
   k_tl_outer<<<vector_blocks(n), 256, 0, st>>>(n, gm, q, w);
 }
 
-void launch_tl_cg_dir(int64_t n, const double* rr_new, const double* rr_old, const float* r,
-                      float* p, cudaStream_t st) {
-  ProfileRange pr(K_PRECOND, (double)n * 12, st);
-  k_tl_cg_dir<<<vector_blocks(n), 256, 0, st>>>(n, rr_new, rr_old, r, p);
-}
 
 static int64_t coarse_half(const Grid& gc) { return (int64_t)gc.n1 * gc.n2 * (gc.n3 / 2 + 1); }
 static unsigned spec_grid(const Grid& gc) { return (unsigned)vector_blocks(coarse_half(gc)); }
@@ -299,45 +319,38 @@ void launch_tl_spec_table(const Grid& gc, float alpha, float gamma, float2* fw, 
   k_tl_spec_table<<<nblk(Ch), 256, 0, st>>>(Ch, gc.n1, gc.n2, gc.n3, alpha, gamma, fw);
 }
 
-void launch_tl_spec_scale(const Grid& gc, const float2* fw, const cufftComplex* in,
-                          cufftComplex* out, float scale, cudaStream_t st) {
-  const int64_t Ch = coarse_half(gc);
-  ProfileRange pr(K_PRECOND, (double)Ch * 3 * 16, st);
-  k_tl_spec_scale<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, in, out, scale);
-}
-
 void launch_tl_spec_finish(const Grid& gc, const float2* fw, const cufftComplex* p,
                            const cufftComplex* y, cufftComplex* Ap, float scale, double* partial,
-                           double* pAp, cudaStream_t st) {
+                           unsigned* count, double* pAp, cudaStream_t st) {
   const int64_t Ch = coarse_half(gc);
-  {
-    ProfileRange pr(K_PRECOND, (double)Ch * 3 * 24, st);
-    k_tl_spec_finish<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, p, y, Ap, scale, partial);
-  }
-  launch_reduce_final(partial, tl_spec_blocks(gc), RED_SUM, pAp, st);
+  ProfileRange pr(K_PRECOND, (double)Ch * 3 * 24, st);
+  k_tl_spec_finish<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, p, y, Ap, scale, partial, count, pAp);
 }
 
 void launch_tl_spec_step(const Grid& gc, const float2* fw, const double* rr, const double* pAp,
                          cufftComplex* x, cufftComplex* r, const cufftComplex* p,
-                         const cufftComplex* Ap, double* partial, double* rr_new,
-                         cudaStream_t st) {
+                         const cufftComplex* Ap, double* partial, unsigned* count,
+                         double* rr_new, cudaStream_t st) {
   const int64_t Ch = coarse_half(gc);
-  {
-    ProfileRange pr(K_PRECOND, (double)Ch * 3 * 48, st);
-    k_tl_spec_step<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, rr, pAp, x, r, p, Ap, partial);
-  }
-  launch_reduce_final(partial, tl_spec_blocks(gc), RED_SUM, rr_new, st);
+  ProfileRange pr(K_PRECOND, (double)Ch * 3 * 48, st);
+  k_tl_spec_step<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, rr, pAp, x, r, p, Ap, partial, count,
+                                                 rr_new);
 }
 
-void launch_tl_spec_init(const Grid& gc, const float2* fw, const cufftComplex* b, cufftComplex* x,
-                         cufftComplex* r, cufftComplex* p, double* partial, double* bb,
-                         cudaStream_t st) {
+void launch_tl_spec_init(const Grid& gc, const float2* fw, cufftComplex* b, cufftComplex* x,
+                         cufftComplex* r, cufftComplex* p, double* partial, unsigned* count,
+                         double* bb, cudaStream_t st) {
   const int64_t Ch = coarse_half(gc);
-  {
-    ProfileRange pr(K_PRECOND, (double)Ch * 3 * 32, st);
-    k_tl_spec_init<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, b, x, r, p, partial);
-  }
-  launch_reduce_final(partial, tl_spec_blocks(gc), RED_SUM, bb, st);
+  ProfileRange pr(K_PRECOND, (double)Ch * 3 * 40, st);
+  k_tl_spec_init<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, b, x, r, p, partial, count, bb);
+}
+
+void launch_tl_dir_scale(const Grid& gc, const float2* fw, const double* rr_new,
+                         const double* rr_old, const cufftComplex* r, cufftComplex* p,
+                         cufftComplex* cc, cudaStream_t st) {
+  const int64_t Ch = coarse_half(gc);
+  ProfileRange pr(K_PRECOND, (double)Ch * 3 * 32, st);
+  k_tl_dir_scale<<<spec_grid(gc), 256, 0, st>>>(Ch, fw, rr_new, rr_old, r, p, cc);
 }
 
 // ---- nested CG driven on the device (a captured graph with a conditional while
