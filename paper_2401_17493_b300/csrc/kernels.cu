@@ -297,10 +297,12 @@ __global__ void __launch_bounds__(256) k_spectral(int n1, int n2, int n3, int64_
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dot = 0.0;
   if (i < Nc) {
-    const int nh = n3 / 2 + 1;
-    const int j3 = (int)(i % nh);
-    const int j2 = (int)((i / nh) % n2);
-    const int j1 = (int)(i / ((int64_t)nh * n2));
+    // Nc < 2^31 (3 N < 2^31): 32-bit index math
+    const unsigned nh = (unsigned)(n3 / 2 + 1), u = (unsigned)i;
+    const unsigned q = u / nh;
+    const int j3 = (int)(u - q * nh);
+    const int j1 = (int)(q / (unsigned)n2);
+    const int j2 = (int)(q - (unsigned)j1 * (unsigned)n2);
     const float k1 = (float)(j1 <= n1 / 2 ? j1 : j1 - n1);
     const float k2 = (float)(j2 <= n2 / 2 ? j2 : j2 - n2);
     const float k3 = (float)j3;

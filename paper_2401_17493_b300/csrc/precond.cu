@@ -21,11 +21,13 @@ struct ModeIdx {
   int64_t ci;          // coarse half-spectrum index (valid when low)
 };
 
+// (i < 2^31: a half spectrum of a grid with 3 N < 2^31, so 32-bit index math)
 __device__ __forceinline__ ModeIdx fine_mode(const Grid& g, int64_t i, int c1n, int c2n) {
-  const int nh = g.n3 / 2 + 1;
-  const int j3 = (int)(i % nh);
-  const int j2 = (int)((i / nh) % g.n2);
-  const int j1 = (int)(i / ((int64_t)nh * g.n2));
+  const unsigned nh = (unsigned)(g.n3 / 2 + 1), u = (unsigned)i;
+  const unsigned q = u / nh;
+  const int j3 = (int)(u - q * nh);
+  const int j1 = (int)(q / (unsigned)g.n2);
+  const int j2 = (int)(q - (unsigned)j1 * (unsigned)g.n2);
   ModeIdx m;
   m.k1 = j1 <= g.n1 / 2 ? j1 : j1 - g.n1;
   m.k2 = j2 <= g.n2 / 2 ? j2 : j2 - g.n2;
@@ -125,10 +127,11 @@ __global__ void k_tl_spec_table(int64_t Ch, int n1, int n2, int n3, float alpha,
                                 float2* __restrict__ fw) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Ch) return;
-  const int nh = n3 / 2 + 1;
-  const int j3 = (int)(i % nh);
-  const int j2 = (int)((i / nh) % n2);
-  const int j1 = (int)(i / ((int64_t)nh * n2));
+  const unsigned nh = (unsigned)(n3 / 2 + 1), u = (unsigned)i;
+  const unsigned q = u / nh;
+  const int j3 = (int)(u - q * nh);
+  const int j1 = (int)(q / (unsigned)n2);
+  const int j2 = (int)(q - (unsigned)j1 * (unsigned)n2);
   const int k1 = j1 <= n1 / 2 ? j1 : j1 - n1;
   const int k2 = j2 <= n2 / 2 ? j2 : j2 - n2;
   fw[i] = make_float2(inv_sqrt_symbol(k1, k2, j3, alpha, gamma),
