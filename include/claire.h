@@ -65,7 +65,10 @@ typedef struct {
                            ||g(v = 0)||_inf computed by the solver (reading C-10)    */
   int autotune;         /* 1: time the tile-shape variants on the first evaluation of a
                            solve and keep the fastest for this context (default 0)   */
-  int graphs;           /* 1: replay each PCG iteration as a captured CUDA graph      */
+  int graphs;           /* 1: replay the parts of PCG (start, H s and update, next
+                           direction) as captured CUDA graphs, the two-level nested CG
+                           inside them as a conditional while node; bitwise the same
+                           results as launch by launch (0, the default)              */
   int precond;          /* PCG preconditioner (Sec. 2.5.6).  0: spectral, (beta_v L)^-1
                            with the zero symbol set to one.  1: two-level
                            zero-velocity H0: R^-1/2 M^-1 R^-1/2 with R = beta_v L, M^-1

@@ -947,7 +947,7 @@ claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
       // nothing of the failed capture ran: run this part (and later ones) uncaptured
       cudaGetLastError();
       if (c->opt.verbose)
-        fprintf(stderr, "[claire] nested CG not captured (%s); PCG part B runs uncaptured\n",
+        fprintf(stderr, "[claire] nested CG not captured (%s); PCG parts S and B run uncaptured\n",
                 c->err.empty() ? cudaGetErrorString(e) : c->err.c_str());
       c->err.clear();
       c->tl_nograph = true;
