@@ -86,8 +86,8 @@ __device__ __forceinline__ int nbr_of(const Vol& s, const Vox& p, int dz, int dy
 // and multiplied, and a buffer is refilled only after the mbarrier reports the
 // MMAs of its previous use done.  The epilogue reads the thread's TMEM lane (its
 // voxel) 16 columns at a time, adds the bias, applies the ReLU and stores BF16
-// and / or FP32.  Every wait is bounded; one that runs out makes the outputs NaN
-// instead of hanging.
+// and / or FP32.  Every wait is bounded; one that runs out ends the CTA's later
+// waits and makes its outputs NaN instead of hanging.
 constexpr int CONV_M = 128;
 constexpr int CONV_S = 4;                         // stage buffers
 constexpr int CONV_L = 2;                         // stages gathered ahead
@@ -162,12 +162,12 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, Vo
   for (int i = 0; i < CONV_L; ++i) gather(i);
   for (int i = 0; i < nstage; ++i) {
     const int j = i + CONV_L;                                  // stage to gather now
-    if (j < nstage && j >= CONV_S)                             // its buffer's previous MMAs
-      ok &= mbar_wait(&mbar[j % CONV_S], ((j - CONV_S) / CONV_S) & 1, CONV_WAIT);
+    if (ok && j < nstage && j >= CONV_S)                       // its buffer's previous MMAs
+      ok = mbar_wait(&mbar[j % CONV_S], ((j - CONV_S) / CONV_S) & 1, CONV_WAIT);
     gather(j);
     asm volatile("cp.async.wait_group %0;\n" ::"n"(CONV_L) : "memory");   // stage i landed
     fence_proxy_async_smem();
-    __syncthreads();
+    ok = __syncthreads_and(ok);          // a timed-out wait ends the waits of the whole CTA
     if (tid == 0) {
       tc_fence_after_sync();
       uint8_t* sa = conv_smem + (i % CONV_S) * (SM::A + SM::B);
@@ -496,6 +496,214 @@ std::vector<ResamplePlan> g_resample_plans;
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Halo-tile variant for volumes with W % 8 == 0 and H % 16 == 0: a CTA owns the
+// 8 (x) x 16 (y) output voxels of one (sample, z) and stages their 10 x 18 x 3
+// input neighbourhood once per group of G 16-channel chunks, in the K-major
+// core-matrix layout [chunk][K half][z'][y'][x'] x 16 bytes.  The A operand of tap
+// (dz, dy, dx) is then a descriptor into that tile: rows of an 8-voxel x run are
+// 16 bytes apart, the 16 runs (y) HALO_TX * 16 bytes apart (the stride byte
+// offset), the two K halves HALO_PLANE * 16 bytes apart (the leading byte
+// offset), starting at the tile row of the tap's first input voxel.  Each input
+// row is copied into shared memory once per CTA instead of 27 times.  With a
+// single chunk group whose 27 taps of weights fit beside the tile (res), the
+// weights are staged with it and one thread issues all 27 x G MMAs behind one
+// barrier; otherwise they stream through four stage buffers, one tap (G MMAs) per
+// stage, and the tile of the next group is staged once the MMAs of the previous
+// one completed.  Output rows: r = 8 y + x, the thread of TMEM lane r writes voxel
+// (x0 + r % 8, y0 + r / 8).
+constexpr int HALO_TX = 10, HALO_TY = 18, HALO_TZ = 3;
+constexpr int HALO_PLANE = HALO_TX * HALO_TY * HALO_TZ;   // 540 voxel rows
+constexpr int HALO_RES_BYTES = 100 * 1024;                // tile + all weights, resident
+template <int N, int G>
+struct HaloSmem {
+  static constexpr int A = G * 2 * HALO_PLANE * 16;       // the input tile of one group
+  static constexpr int B = G * N * 32;                     // the weights of one tap
+  static constexpr bool res_fits = A + 27 * B <= HALO_RES_BYTES;
+  static constexpr int bytes = A + (res_fits ? 27 : CONV_S) * B;
+};
+
+template <int N, int G>
+__global__ void __launch_bounds__(128) k_conv_fwd_halo(const bf16* __restrict__ X, Vol s,
+                                                       int Cin, const bf16* __restrict__ Wt,
+                                                       const float* __restrict__ bias,
+                                                       int Cout, int relu,
+                                                       bf16* __restrict__ Y,
+                                                       float* __restrict__ Y32) {
+  using SM = HaloSmem<N, G>;
+  constexpr uint32_t NCOL = N < 32 ? 32 : N;
+  extern __shared__ __align__(128) uint8_t conv_smem[];
+  __shared__ __align__(8) uint64_t mbar[CONV_S];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int n0 = blockIdx.y * N;
+  const int groups = Cin / (16 * G);
+  const bool res = SM::res_fits && groups == 1;
+  // CTA -> (sample, z, y block, x block)
+  const int xb = s.W / 8, yb = s.H / 16;
+  int q = blockIdx.x;
+  const int x0 = (q % xb) * 8;
+  q /= xb;
+  const int y0 = (q % yb) * 16;
+  q /= yb;
+  const int z = q % s.D, b = q / s.D;
+  uint8_t* tile = conv_smem;
+  uint8_t* bbuf = conv_smem + SM::A;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, NCOL);
+    tmem_relinquish();
+  }
+  if (tid == 0)
+    for (int k = 0; k < CONV_S; ++k) mbar_init(&mbar[k], 1);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = umma_idesc_bf16(CONV_M, N);
+  // the input tile of chunk group g, periodic in x, y, z
+  auto stage_tile = [&](int g) {
+    for (int j = tid; j < HALO_PLANE * G * 2; j += 128) {
+      const int vr = j % HALO_PLANE, ch = j / HALO_PLANE;    // ch = 2 chunk + K half
+      const int xp = vr % HALO_TX, yp = (vr / HALO_TX) % HALO_TY,
+                zp = vr / (HALO_TX * HALO_TY);
+      int x = x0 - 1 + xp, y = y0 - 1 + yp, zz = z - 1 + zp;
+      x = x < 0 ? x + s.W : (x >= s.W ? x - s.W : x);
+      y = y < 0 ? y + s.H : (y >= s.H ? y - s.H : y);
+      zz = zz < 0 ? zz + s.D : (zz >= s.D ? zz - s.D : zz);
+      const int64_t src =
+          ((int64_t)((b * s.D + zz) * s.H + y) * s.W + x) * Cin + g * G * 16 + ch * 8;
+      cp_async16_ca(tile + (ch * HALO_PLANE + vr) * 16, X + src);
+    }
+  };
+  // weights of tap t, chunk group g, into buffer dst
+  auto stage_tap = [&](int t, int g, uint8_t* dst) {
+    for (int j = tid; j < G * 2 * N; j += 128) {
+      const int c = j / (2 * N), r = j - c * 2 * N;
+      const int n = r >> 1, h = r & 1;
+      cp_async16_ca(dst + c * (N * 32) + h * (N * 16) + (n >> 3) * 128 + (n & 7) * 16,
+                    Wt + ((int64_t)(n0 + n) * 27 + t) * Cin + (g * G + c) * 16 + h * 8);
+    }
+  };
+  // the G MMAs of tap t, B from buffer src; the first MMA of the call overwrites D
+  auto mma_tap = [&](int t, const uint8_t* src, bool first) {
+    const int tap = (t / 9) * (HALO_TX * HALO_TY) + ((t / 3) % 3) * HALO_TX + t % 3;
+#pragma unroll
+    for (int c = 0; c < G; ++c)
+      umma_bf16(tmem,
+                umma_smem_desc(tile + (c * 2 * HALO_PLANE + tap) * 16, HALO_PLANE * 16,
+                               HALO_TX * 16),
+                umma_smem_desc(src + c * (N * 32), N * 16, 128), idesc,
+                (first && c == 0) ? 0u : 1u);
+  };
+  bool ok = true;
+  int last = 0;                                                // index of the last commit
+  if (res) {
+    stage_tile(0);
+    for (int t = 0; t < 27; ++t) stage_tap(t, 0, bbuf + t * SM::B);
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after_sync();
+      for (int t = 0; t < 27; ++t) mma_tap(t, bbuf + t * SM::B, t == 0);
+      umma_commit(&mbar[0]);
+    }
+  } else {
+    const int nstage = 27 * groups;                            // (group, tap), taps inner
+    auto gather = [&](int i) {
+      if (i < nstage) {
+        if (i % 27 == 0) stage_tile(i / 27);                   // the group's first stage
+        stage_tap(i % 27, i / 27, bbuf + (i % CONV_S) * SM::B);
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    for (int i = 0; i < nstage; ++i) {
+      // a group's tile replaces the previous one once all its MMAs completed
+      if (ok && i % 27 == 0 && i > 0)
+        ok = mbar_wait(&mbar[(i - 1) % CONV_S], ((i - 1) / CONV_S) & 1, CONV_WAIT);
+      if (i % 27 == 0) {
+        ok = __syncthreads_and(ok);
+        for (int k = 0; k < CONV_L; ++k) gather(i + k);
+      }
+      const int j = i + CONV_L;                                // stage to gather now
+      if (ok && j < nstage && j % 27 >= CONV_L && j >= CONV_S)
+        ok = mbar_wait(&mbar[j % CONV_S], ((j - CONV_S) / CONV_S) & 1, CONV_WAIT);
+      if (j % 27 >= CONV_L) gather(j);                         // else: the next group's
+      else asm volatile("cp.async.commit_group;\n" ::: "memory");   // first stages wait
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(CONV_L) : "memory");
+      fence_proxy_async_smem();
+      ok = __syncthreads_and(ok);        // a timed-out wait ends the waits of the whole CTA
+      if (tid == 0) {
+        tc_fence_after_sync();
+        mma_tap(i % 27, bbuf + (i % CONV_S) * SM::B, i == 0);
+        umma_commit(&mbar[i % CONV_S]);
+      }
+    }
+    last = nstage - 1;
+  }
+  ok &= mbar_wait(&mbar[last % CONV_S], (last / CONV_S) & 1, CONV_WAIT);
+  tc_fence_after_sync();
+  const int64_t v = ((int64_t)(b * s.D + z) * s.H + y0 + (tid >> 3)) * s.W + x0 + (tid & 7);
+#pragma unroll 1
+  for (int c = 0; c < N; c += 16) {
+    float y[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, y);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      float t = y[e] + (bias ? bias[n0 + c + e] : 0.f);
+      if (relu) t = fmaxf(t, 0.f);
+      y[e] = ok ? t : __int_as_float(0x7fc00000);
+    }
+    if (Y) {
+      uint32_t w[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        w[e] = pack_bf16(__float2bfloat16_rn(y[2 * e]), __float2bfloat16_rn(y[2 * e + 1]));
+      uint4* dst = reinterpret_cast<uint4*>(Y + v * Cout + n0 + c);
+      dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    if (Y32) {
+      float4* dst = reinterpret_cast<float4*>(Y32 + v * Cout + n0 + c);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        dst[e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
+    }
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NCOL);
+}
+
+template <int N, int G>
+void launch_conv_fwd_halo_g(cudaStream_t st, const bf16* X, const Vol& s, int cin,
+                            const bf16* Wt, const float* bias, int cout, int relu, bf16* Y,
+                            float* Y32) {
+  constexpr int bytes = HaloSmem<N, G>::bytes;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_conv_fwd_halo<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
+    return true;
+  }();
+  (void)attr;
+  const dim3 grid(s.B * s.D * (s.H / 16) * (s.W / 8), cout / N);
+  k_conv_fwd_halo<N, G><<<grid, 128, bytes, st>>>(X, s, cin, Wt, bias, cout, relu, Y, Y32);
+}
+
+// The halo-tile kernel where it applies (W % 8 == 0, H % 16 == 0); chunk groups of
+// G = the largest of 4, 3, 2, 1 that divides the 16-channel chunks.
+template <int N>
+bool launch_conv_fwd_halo(cudaStream_t st, const bf16* X, const Vol& s, int cin,
+                          const bf16* Wt, const float* bias, int cout, int relu, bf16* Y,
+                          float* Y32) {
+  if (s.W % 8 || s.H % 16) return false;
+  const int chunks = cin / 16;
+  if (chunks % 4 == 0) launch_conv_fwd_halo_g<N, 4>(st, X, s, cin, Wt, bias, cout, relu, Y, Y32);
+  else if (chunks % 3 == 0) launch_conv_fwd_halo_g<N, 3>(st, X, s, cin, Wt, bias, cout, relu, Y, Y32);
+  else if (chunks % 2 == 0) launch_conv_fwd_halo_g<N, 2>(st, X, s, cin, Wt, bias, cout, relu, Y, Y32);
+  else launch_conv_fwd_halo_g<N, 1>(st, X, s, cin, Wt, bias, cout, relu, Y, Y32);
+  return true;
+}
+
 template <int N, int KC>
 void launch_conv_fwd_kc(dim3 grid, cudaStream_t st, const bf16* X, const Vol& s, int cin,
                         const bf16* Wt, const float* bias, int cout, int relu, bf16* Y,
@@ -516,6 +724,7 @@ void launch_conv_fwd_kc(dim3 grid, cudaStream_t st, const bf16* X, const Vol& s,
 template <int N>
 void launch_conv_fwd(dim3 grid, cudaStream_t st, const bf16* X, const Vol& s, int cin,
                      const bf16* Wt, const float* bias, int cout, int relu, bf16* Y, float* Y32) {
+  if (launch_conv_fwd_halo<N>(st, X, s, cin, Wt, bias, cout, relu, Y, Y32)) return;
   const int chunks = cin / 16;
   const int kc_max = CONV_STAGE_BYTES / (CONV_M * 32 + N * 32);
   int kc = 1;

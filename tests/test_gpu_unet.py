@@ -50,8 +50,14 @@ def _to_cl(x):
         torch.bfloat16).cuda()
 
 
+# shapes with H % 16 == 0 and W % 8 == 0 take the halo-tile forward kernel (one
+# chunk group, weights resident or streamed; several groups for 96 input channels
+# and, in the data gradient, 80 and 128), the first three the per-tap gather kernel
 @pytest.mark.parametrize("cin,cout,shape", [(16, 16, (8, 6, 10)), (48, 32, (6, 6, 6)),
-                                            (32, 64, (4, 8, 4))])
+                                            (32, 64, (4, 8, 4)), (16, 16, (4, 16, 8)),
+                                            (48, 16, (3, 16, 16)), (64, 32, (2, 32, 8)),
+                                            (32, 128, (5, 16, 24)), (16, 80, (2, 16, 8)),
+                                            (96, 32, (3, 16, 8))])
 def test_conv_forward_dgrad_wgrad_match_oracle(lib, cin, cout, shape):
     rng = np.random.default_rng(cin + cout)
     x = _bf(rng.standard_normal((cin,) + shape))
@@ -84,9 +90,10 @@ def test_conv_forward_dgrad_wgrad_match_oracle(lib, cin, cout, shape):
     assert rel(np.transpose(dw.cpu().numpy(), (0, 2, 1)), OC.conv3d_weight_grad(x, dy)) < 1e-4
 
 
-def test_conv_batch_and_ragged_voxel_count(lib):
+@pytest.mark.parametrize("B,D,H,W,cin,cout", [(3, 6, 6, 6, 16, 16),      # V = 648, ragged
+                                              (2, 4, 16, 8, 32, 16)])    # halo-tile kernel
+def test_conv_batch_and_ragged_voxel_count(lib, B, D, H, W, cin, cout):
     rng = np.random.default_rng(7)
-    B, D, H, W, cin, cout = 3, 6, 6, 6, 16, 16          # V = 648, not a multiple of 64
     xs = [_bf(rng.standard_normal((cin, D, H, W))) for _ in range(B)]
     w = _bf(rng.standard_normal((cout, cin, 27)) * 0.2)
     xg = torch.cat([_to_cl(x) for x in xs])
