@@ -299,9 +299,12 @@ claire_status claire_conv3d_forward(const void* x, int B, int D, int H, int W, i
  * claire_conv3d_forward of dy with wf (cin and cout swapped, no bias / ReLU). */
 claire_status claire_conv3d_flip_weights(const void* w, int cout, int cin, void* wf,
                                          void* stream);
-/* Weight gradient dw[cout][27][cin] (FP32) = sum_v dy[v][n] x[nbr_t(v)][c], as
- * nsplit voxel chunks written to partial (nsplit x cout x 27 x cin floats) and
- * summed in a fixed order.  cin in {16, 32, 48, 64, 96, 128, 192}. */
+/* Weight gradient dw[cout][27][cin] (FP32) = sum_v dy[v][n] x[nbr_t(v)][c], as at
+ * most nsplit partial sums written to partial (room for nsplit x cout x 27 x cin
+ * floats) and added in a fixed order.  cin in {16, 32, 48, 64, 96, 128, 192}.
+ * With W % 8 == 0, H % 16 == 0 and cin <= cout <= 128 it runs on the tcgen05
+ * tensor cores (min(nsplit, SMs, 8 x 16-voxel tiles) persistent CTAs, one partial
+ * each), otherwise on mma.sync over voxel chunks of at least 4096 voxels. */
 claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int cin,
                                   const void* dy, int cout, float* partial, int nsplit,
                                   float* dw, void* stream);

@@ -43,7 +43,7 @@ def main():
         b = torch.zeros(cout, device="cuda")
         y = torch.empty(V, cout, device="cuda", dtype=torch.bfloat16)
         dy = (torch.randn(V, cout, device="cuda", generator=gen) * 0.1).to(torch.bfloat16)
-        nsplit = max(1, min(256, V // 4096))
+        nsplit = max(1, min(160, V // 128))             # >= one weight-gradient CTA per SM
         part = torch.empty(nsplit * cout * 27 * cin, device="cuda")
         dw = torch.empty(cout * 27 * cin, device="cuda")
 

@@ -290,6 +290,125 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, 
   }
 }
 
+// Weight gradient on the tensor cores (tcgen05) for volumes with W % 8 == 0,
+// H % 16 == 0 and Cout <= 128, one group of 16 input channels per blockIdx.y:
+//   dW[co][t][ci] = sum_v dY[v][co] X[v + off(t)][ci]
+// as D[co][(t, ci)] += A[co][v] B_t[ci][v] with M = 128 (co, rows >= Cout zero),
+// N = 16, K = voxels.  A persistent CTA walks 8 x 16-voxel tiles of one (sample, z)
+// (the tiles blockIdx.x, blockIdx.x + gridDim.x, ...), accumulating all 27 taps in
+// 432 TMEM columns; per tile it stages A = dY transposed, [y][co][x] x 2 bytes
+// (K-major: 8-voxel x runs are the 16-byte K rows), and the input neighbourhood
+// transposed once per x shift, XT[dx][z'][y'][ci][x] (so every tap's B is 16-byte
+// aligned), then one thread issues 27 taps x 8 MMAs (K = 16: two y rows each).  The
+// CTA's partial dW goes to part[blockIdx.x]; k_sum_partials adds them in order.
+// Every wait is bounded; a timed-out one makes the CTA's partial NaN.
+constexpr int WG_A = 16 * 128 * 16;                       // A: 16 y x 128 co x 8 x
+constexpr int WG_XT = 3 * 3 * 18 * 16 * 16;               // XT: 3 dx x 3 z x 18 y x 16 ci x 8 x
+// requested dynamic shared memory: more than half an SM's, so that one CTA (holding
+// all 512 TMEM columns) runs per SM
+constexpr int WG_SMEM = 120 * 1024;
+static_assert(WG_A + WG_XT <= WG_SMEM, "weight-gradient buffers");
+__global__ void __launch_bounds__(128) k_conv_wgrad_tc(const bf16* __restrict__ X, Vol s,
+                                                       int Cin, const bf16* __restrict__ dY,
+                                                       int Cout, float* __restrict__ part) {
+  extern __shared__ __align__(128) uint8_t wg_smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = blockIdx.y;                                  // input channels 16 g .. 16 g + 15
+  uint8_t* A = wg_smem;
+  uint8_t* XT = wg_smem + WG_A;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) mbar_init(&mbar, 1);
+  // rows co >= Cout of A stay zero
+  for (int i = tid; i < WG_A / 16; i += 128) reinterpret_cast<uint4*>(A)[i] = make_uint4(0, 0, 0, 0);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = umma_idesc_bf16(CONV_M, 16);
+  const int xb = s.W / 8, yb = s.H / 16;
+  const int ntiles = s.B * s.D * yb * xb;
+  bool ok = true;
+  int it = 0;
+  for (int q0 = blockIdx.x; q0 < ntiles && ok; q0 += gridDim.x, ++it) {
+    int q = q0;
+    const int x0 = (q % xb) * 8;
+    q /= xb;
+    const int y0 = (q % yb) * 16;
+    q /= yb;
+    const int z = q % s.D, b = q / s.D;
+    // A[y][co][x] = dY[(x0 + x, y0 + y)][co]
+    for (int i = tid; i < 128 * (Cout / 8); i += 128) {
+      const int vl = i & 127, c8 = i >> 7;
+      const int y = vl >> 3, x = vl & 7;
+      const int64_t v = ((int64_t)(b * s.D + z) * s.H + y0 + y) * s.W + x0 + x;
+      const uint4 d = *reinterpret_cast<const uint4*>(dY + v * Cout + c8 * 8);
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        *reinterpret_cast<uint16_t*>(A + ((y * 128 + c8 * 8 + e) * 8 + x) * 2) = h[e];
+    }
+    // XT[dxi][zp][yp][ci][x] = X[(x0 + x + dxi - 1, y0 + yp - 1, z + zp - 1)][16 g + ci]
+    for (int i = tid; i < 3 * 3 * 18 * 8 * 2; i += 128) {
+      const int hh = i & 1;
+      int r = i >> 1;
+      const int x = r & 7;
+      r >>= 3;
+      const int yp = r % 18;
+      r /= 18;
+      const int zp = r % 3, dxi = r / 3;
+      int xx = x0 + x + dxi - 1, yy = y0 + yp - 1, zz = z + zp - 1;
+      xx = xx < 0 ? xx + s.W : (xx >= s.W ? xx - s.W : xx);
+      yy = yy < 0 ? yy + s.H : (yy >= s.H ? yy - s.H : yy);
+      zz = zz < 0 ? zz + s.D : (zz >= s.D ? zz - s.D : zz);
+      const int64_t v = ((int64_t)(b * s.D + zz) * s.H + yy) * s.W + xx;
+      const uint4 d = *reinterpret_cast<const uint4*>(X + v * Cin + g * 16 + hh * 8);
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
+      uint8_t* row = XT + ((((dxi * 3 + zp) * 18 + yp) * 16 + hh * 8) * 8 + x) * 2;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) *reinterpret_cast<uint16_t*>(row + e * 16) = h[e];
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after_sync();
+      for (int t = 0; t < 27; ++t) {
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;   // offsets + 1
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          umma_bf16(tmem + (uint32_t)(t * 16),
+                    umma_smem_desc(A + j * 2 * 2048, 2048, 128),
+                    umma_smem_desc(XT + ((dx * 3 + dz) * 18 + 2 * j + dy) * 256, 256, 128),
+                    idesc, (it > 0 || j > 0) ? 1u : 0u);
+      }
+      umma_commit(&mbar);
+    }
+    ok = mbar_wait(&mbar, it & 1, CONV_WAIT);                // the buffers are free again
+    ok = __syncthreads_and(ok);
+  }
+  tc_fence_after_sync();
+  const int co = warp * 32 + (tid & 31);
+#pragma unroll 1
+  for (int t = 0; t < 27; ++t) {
+    float y[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 16), y);
+    if (co >= Cout) continue;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) y[e] = !ok ? __int_as_float(0x7fc00000) : (it > 0 ? y[e] : 0.f);
+    float4* dst = reinterpret_cast<float4*>(
+        part + (((int64_t)blockIdx.x * Cout + co) * 27 + t) * Cin + g * 16);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dst[e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 __global__ void k_sum_partials(const float* __restrict__ part, int nsplit, int64_t n,
                                float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -793,7 +912,32 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
   const Vol s{B, D, H, W};
   const int64_t V = (int64_t)B * D * H * W;
   if (V >= INT32_MAX) return CLAIRE_EINVAL;
-  int64_t chunk = (V + nsplit - 1) / nsplit;
+  cudaStream_t st0 = (cudaStream_t)stream;
+  if (W % 8 == 0 && H % 16 == 0 && cout <= 128 && cin <= cout) {
+    // tensor-core path: one persistent CTA per SM (each holds all 512 TMEM columns).
+    // Measured faster than the mma.sync kernel where cin <= cout (16 -> 16 at 64^3:
+    // 718 vs 957 us); with more input than output channels the 128-row padding of
+    // the output channels and one pass per 16 input channels make it slower.
+    static int nsm = 0;
+    if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
+      return CLAIRE_ECUDA;
+    static const bool attr = [] {
+      cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           WG_SMEM);
+      return true;
+    }();
+    (void)attr;
+    const int ntiles = B * D * (H / 16) * (W / 8);
+    const int ncta = std::max(1, std::min(std::min(nsplit, nsm), ntiles));
+    k_conv_wgrad_tc<<<dim3(ncta, cin / 16), 128, WG_SMEM, st0>>>(
+        (const bf16*)x, s, cin, (const bf16*)dy, cout, partial);
+    const int64_t n = (int64_t)cout * 27 * cin;
+    k_sum_partials<<<blocks(n), 256, 0, st0>>>(partial, ncta, n, dw);
+    return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
+  }
+  // mma.sync path: chunks of at least 4096 voxels (more splits only add partials to sum)
+  const int64_t nsp = std::max<int64_t>(1, std::min<int64_t>(nsplit, V / 4096));
+  int64_t chunk = (V + nsp - 1) / nsp;
   chunk = ((chunk + 63) / 64) * 64;
   const int ns = (int)((V + chunk - 1) / chunk);
   const dim3 grid(ns, 27, cout / 16);

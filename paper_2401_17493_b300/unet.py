@@ -40,6 +40,12 @@ PRECOND = 1         # registration solves: two-level zero-velocity preconditione
 MAX_INNER = 10      # nested CG cap of that preconditioner
 
 
+def wgrad_splits(V):
+    """Voxel splits of a weight gradient over V voxels (its partial buffer holds this
+    many copies of dW): at least one tensor-core weight-gradient CTA per SM."""
+    return max(1, min(160, V // 128))
+
+
 def _p(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
@@ -90,7 +96,7 @@ class Conv:
         if self.relu:
             _check(L.claire_unet_op(0, _p(y), _p(dy), V, self.cout, 0, 0, 0, 0, 0, 0, s),
                    "relu_bwd")
-        nsplit = max(1, min(256, V // 4096))
+        nsplit = wgrad_splits(V)
         need = nsplit * self.cout * 27 * self.cin
         if partial is None or partial.numel() < need:
             raise ValueError("wgrad partial buffer too small")
@@ -221,7 +227,7 @@ class UNet3D:
                                                 ctypes.c_void_p(self.partial.data_ptr() + 8 * nb),
                                                 _stream()), "mse")
         loss = self.partial[nb]
-        need = max(max(1, min(256, V // 4096)) * l.cout * 27 * l.cin
+        need = max(wgrad_splits(V) * l.cout * 27 * l.cin
                    for l, V in [(L[k], Vs[lv]) for k, lv in LAYER_LEVEL.items()])
         if self.wpart is None or self.wpart.numel() < need:
             self.wpart = torch.empty(need, device="cuda")

@@ -93,6 +93,30 @@ def test_conv_forward_dgrad_wgrad_match_oracle(lib, cin, cout, shape):
 @pytest.mark.parametrize("B,D,H,W,cin,cout", [(3, 6, 6, 6, 16, 16),      # V = 648, ragged
                                               (2, 4, 16, 8, 32, 16)])    # halo-tile kernel
 def test_conv_batch_and_ragged_voxel_count(lib, B, D, H, W, cin, cout):
+    _batch_case(lib, B, D, H, W, cin, cout)
+
+
+def test_tensor_core_weight_gradient_on_many_tiles(lib):
+    """The tcgen05 weight gradient with persistent CTAs that each accumulate several
+    8 x 16 tiles (128 tiles over 32 CTAs) against the FP64 oracle."""
+    rng = np.random.default_rng(11)
+    B, D, H, W, cin, cout = 2, 8, 32, 32, 32, 48
+    xs = [_bf(rng.standard_normal((cin, D, H, W))) for _ in range(B)]
+    dys = [_bf(rng.standard_normal((cout, D, H, W))) for _ in range(B)]
+    xg = torch.cat([_to_cl(x) for x in xs])
+    dyg = torch.cat([_to_cl(d) for d in dys])
+    nsplit = 32
+    part = torch.empty(nsplit * cout * 27 * cin, device="cuda")
+    dw = torch.empty((cout, 27, cin), device="cuda")
+    L = lib.load_library()
+    assert L.claire_conv3d_wgrad(_p(xg), B, D, H, W, cin, _p(dyg), cout, _p(part), nsplit,
+                                 _p(dw), None) == 0
+    torch.cuda.synchronize()
+    ref = sum(OC.conv3d_weight_grad(x, d) for x, d in zip(xs, dys))
+    assert rel(np.transpose(dw.cpu().numpy(), (0, 2, 1)), ref) < 1e-4
+
+
+def _batch_case(lib, B, D, H, W, cin, cout):
     rng = np.random.default_rng(7)
     xs = [_bf(rng.standard_normal((cin, D, H, W))) for _ in range(B)]
     w = _bf(rng.standard_normal((cout, cin, 27)) * 0.2)
