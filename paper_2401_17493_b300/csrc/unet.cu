@@ -291,40 +291,51 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, 
 }
 
 // Weight gradient on the tensor cores (tcgen05) for volumes with W % 8 == 0,
-// H % 16 == 0 and Cout <= 128, one group of 16 input channels per blockIdx.y:
+// H % 16 == 0 and cin <= cout <= 128, one group of 16 input channels per blockIdx.y:
 //   dW[co][t][ci] = sum_v dY[v][co] X[v + off(t)][ci]
 // as D[co][(t, ci)] += A[co][v] B_t[ci][v] with M = 128 (co, rows >= Cout zero),
 // N = 16, K = voxels.  A persistent CTA walks 8 x 16-voxel tiles of one (sample, z)
 // (the tiles blockIdx.x, blockIdx.x + gridDim.x, ...), accumulating all 27 taps in
-// 432 TMEM columns; per tile it stages A = dY transposed, [y][co][x] x 2 bytes
+// 432 TMEM columns.  Per tile it stages A = dY transposed, [y][co][x] x 2 bytes
 // (K-major: 8-voxel x runs are the 16-byte K rows), and the input neighbourhood
-// transposed once per x shift, XT[dx][z'][y'][ci][x] (so every tap's B is 16-byte
-// aligned), then one thread issues 27 taps x 8 MMAs (K = 16: two y rows each).  The
-// CTA's partial dW goes to part[blockIdx.x]; k_sum_partials adds them in order.
-// Every wait is bounded; a timed-out one makes the CTA's partial NaN.
-constexpr int WG_A = 16 * 128 * 16;                       // A: 16 y x 128 co x 8 x
-constexpr int WG_XT = 3 * 3 * 18 * 16 * 16;               // XT: 3 dx x 3 z x 18 y x 16 ci x 8 x
-// requested dynamic shared memory: more than half an SM's, so that one CTA (holding
-// all 512 TMEM columns) runs per SM
-constexpr int WG_SMEM = 120 * 1024;
-static_assert(WG_A + WG_XT <= WG_SMEM, "weight-gradient buffers");
-__global__ void __launch_bounds__(128) k_conv_wgrad_tc(const bf16* __restrict__ X, Vol s,
-                                                       int Cin, const bf16* __restrict__ dY,
-                                                       int Cout, float* __restrict__ part) {
+// transposed once per x shift, XT[dx][z'][y'][ci][x] (so every tap's B operand is
+// 16-byte aligned); one thread issues 27 taps x 8 MMAs (K = 16: two y rows each)
+// while the CTA stages the next tile into the other of two buffers.  The CTA's
+// partial dW goes to part[blockIdx.x]; k_sum_partials adds them in order.  Every
+// wait is bounded; a timed-out one makes the CTA's partial NaN.
+// A: 16 y x (128 co x 8 x + 16 bytes): the padding of the y pitch (the leading byte
+// offset) and of the XT block pitch spreads the staging stores over all banks
+constexpr int WG_AP = 128 * 16 + 16;                      // 2064 bytes per y
+constexpr int WG_XP = 16 * 16 + 16;                       // 272 bytes per (dx, z, y) block
+constexpr int WG_A = 16 * WG_AP;
+constexpr int WG_XT = 3 * 3 * 18 * WG_XP;                 // XT: 3 dx x 3 z x 18 y blocks
+constexpr int WG_BUF = WG_A + WG_XT;                      // one tile's operands
+// two buffers; more than half an SM's shared memory, so that one CTA (holding all 512
+// TMEM columns) runs per SM
+constexpr int WG_SMEM = 2 * WG_BUF;
+static_assert(WG_SMEM > 114 * 1024 && WG_SMEM <= 227 * 1024, "weight-gradient buffers");
+constexpr int WG_THREADS = 256;
+__global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __restrict__ X, Vol s,
+                                                              int Cin,
+                                                              const bf16* __restrict__ dY,
+                                                              int Cout,
+                                                              float* __restrict__ part) {
   extern __shared__ __align__(128) uint8_t wg_smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int g = blockIdx.y;                                  // input channels 16 g .. 16 g + 15
-  uint8_t* A = wg_smem;
-  uint8_t* XT = wg_smem + WG_A;
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
     tmem_relinquish();
   }
-  if (tid == 0) mbar_init(&mbar, 1);
-  // rows co >= Cout of A stay zero
-  for (int i = tid; i < WG_A / 16; i += 128) reinterpret_cast<uint4*>(A)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  // rows co >= Cout of A (and the pitch padding) stay zero in both buffers
+  for (int i = tid; i < WG_SMEM / 16; i += WG_THREADS)
+    reinterpret_cast<uint4*>(wg_smem)[i] = make_uint4(0, 0, 0, 0);
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
@@ -332,17 +343,18 @@ __global__ void __launch_bounds__(128) k_conv_wgrad_tc(const bf16* __restrict__ 
   constexpr uint32_t idesc = umma_idesc_bf16(CONV_M, 16);
   const int xb = s.W / 8, yb = s.H / 16;
   const int ntiles = s.B * s.D * yb * xb;
-  bool ok = true;
-  int it = 0;
-  for (int q0 = blockIdx.x; q0 < ntiles && ok; q0 += gridDim.x, ++it) {
-    int q = q0;
+  // the operands of tile q into buffer buf
+  auto stage = [&](int q, int buf) {
+    uint8_t* A = wg_smem + buf * WG_BUF;
+    uint8_t* XT = A + WG_A;
     const int x0 = (q % xb) * 8;
     q /= xb;
     const int y0 = (q % yb) * 16;
     q /= yb;
     const int z = q % s.D, b = q / s.D;
-    // A[y][co][x] = dY[(x0 + x, y0 + y)][co]
-    for (int i = tid; i < 128 * (Cout / 8); i += 128) {
+    // A[y][co][x] = dY[(x0 + x, y0 + y)][co]; a warp's lanes take 8 x by 4 y
+#pragma unroll 2
+    for (int i = tid; i < 128 * (Cout / 8); i += WG_THREADS) {
       const int vl = i & 127, c8 = i >> 7;
       const int y = vl >> 3, x = vl & 7;
       const int64_t v = ((int64_t)(b * s.D + z) * s.H + y0 + y) * s.W + x0 + x;
@@ -350,17 +362,15 @@ __global__ void __launch_bounds__(128) k_conv_wgrad_tc(const bf16* __restrict__ 
       const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
 #pragma unroll
       for (int e = 0; e < 8; ++e)
-        *reinterpret_cast<uint16_t*>(A + ((y * 128 + c8 * 8 + e) * 8 + x) * 2) = h[e];
+        *reinterpret_cast<uint16_t*>(A + y * WG_AP + (c8 * 8 + e) * 16 + x * 2) = h[e];
     }
-    // XT[dxi][zp][yp][ci][x] = X[(x0 + x + dxi - 1, y0 + yp - 1, z + zp - 1)][16 g + ci]
-    for (int i = tid; i < 3 * 3 * 18 * 8 * 2; i += 128) {
-      const int hh = i & 1;
-      int r = i >> 1;
-      const int x = r & 7;
-      r >>= 3;
-      const int yp = r % 18;
-      r /= 18;
-      const int zp = r % 3, dxi = r / 3;
+    // XT[dxi][zp][yp][ci][x] = X[(x0 + x + dxi - 1, y0 + yp - 1, z + zp - 1)][16 g + ci];
+    // a warp's lanes take 8 x by 4 consecutive (dxi, zp, yp) blocks
+#pragma unroll 4
+    for (int i = tid; i < 2 * 164 * 8; i += WG_THREADS) {
+      const int x = i & 7, blk = ((i >> 5) % 41) * 4 + ((i >> 3) & 3), hh = (i >> 5) / 41;
+      if (blk >= 3 * 3 * 18) continue;
+      const int yp = blk % 18, zp = (blk / 18) % 3, dxi = blk / 54;
       int xx = x0 + x + dxi - 1, yy = y0 + yp - 1, zz = z + zp - 1;
       xx = xx < 0 ? xx + s.W : (xx >= s.W ? xx - s.W : xx);
       yy = yy < 0 ? yy + s.H : (yy >= s.H ? yy - s.H : yy);
@@ -368,41 +378,58 @@ __global__ void __launch_bounds__(128) k_conv_wgrad_tc(const bf16* __restrict__ 
       const int64_t v = ((int64_t)(b * s.D + zz) * s.H + yy) * s.W + xx;
       const uint4 d = *reinterpret_cast<const uint4*>(X + v * Cin + g * 16 + hh * 8);
       const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
-      uint8_t* row = XT + ((((dxi * 3 + zp) * 18 + yp) * 16 + hh * 8) * 8 + x) * 2;
+      uint8_t* row = XT + blk * WG_XP + hh * 8 * 16 + x * 2;
 #pragma unroll
       for (int e = 0; e < 8; ++e) *reinterpret_cast<uint16_t*>(row + e * 16) = h[e];
     }
     fence_proxy_async_smem();
-    __syncthreads();
+  };
+  bool ok = true;
+  int it = 0;
+  if ((int)blockIdx.x < ntiles) stage(blockIdx.x, 0);
+  ok = __syncthreads_and(ok);
+  for (int q0 = blockIdx.x; q0 < ntiles && ok; q0 += gridDim.x, ++it) {
+    const int buf = it & 1;
     if (tid == 0) {
       tc_fence_after_sync();
+      const uint8_t* A = wg_smem + buf * WG_BUF;
+      const uint8_t* XT = A + WG_A;
       for (int t = 0; t < 27; ++t) {
         const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;   // offsets + 1
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          umma_bf16(tmem + (uint32_t)(t * 16),
-                    umma_smem_desc(A + j * 2 * 2048, 2048, 128),
-                    umma_smem_desc(XT + ((dx * 3 + dz) * 18 + 2 * j + dy) * 256, 256, 128),
+          umma_bf16(tmem + (uint32_t)(t * 16), umma_smem_desc(A + j * 2 * WG_AP, WG_AP, 128),
+                    umma_smem_desc(XT + ((dx * 3 + dz) * 18 + 2 * j + dy) * WG_XP, WG_XP, 128),
                     idesc, (it > 0 || j > 0) ? 1u : 0u);
       }
-      umma_commit(&mbar);
+      umma_commit(&mbar[buf]);
     }
-    ok = mbar_wait(&mbar, it & 1, CONV_WAIT);                // the buffers are free again
-    ok = __syncthreads_and(ok);
+    const int q1 = q0 + gridDim.x;
+    if (q1 < ntiles) {
+      // the other buffer was read by the MMAs of tile it - 1
+      if (it >= 1) ok = mbar_wait(&mbar[buf ^ 1], ((it - 1) >> 1) & 1, CONV_WAIT);
+      if (ok) stage(q1, buf ^ 1);
+    }
+    ok = __syncthreads_and(ok);          // a timed-out wait ends the loop of the whole CTA
   }
+  if (it > 0) ok &= mbar_wait(&mbar[(it - 1) & 1], ((it - 1) >> 1) & 1, CONV_WAIT);
   tc_fence_after_sync();
-  const int co = warp * 32 + (tid & 31);
+  if (warp < 4) {                                            // TMEM lanes 0..127 = co
+    const int co = warp * 32 + (tid & 31);
 #pragma unroll 1
-  for (int t = 0; t < 27; ++t) {
-    float y[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 16), y);
-    if (co >= Cout) continue;
+    for (int t = 0; t < 27; ++t) {
+      float y[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 16), y);
+      if (co >= Cout) continue;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) y[e] = !ok ? __int_as_float(0x7fc00000) : (it > 0 ? y[e] : 0.f);
-    float4* dst = reinterpret_cast<float4*>(
-        part + (((int64_t)blockIdx.x * Cout + co) * 27 + t) * Cin + g * 16);
+      for (int e = 0; e < 16; ++e)
+        y[e] = !ok ? __int_as_float(0x7fc00000) : (it > 0 ? y[e] : 0.f);
+      float4* dst = reinterpret_cast<float4*>(
+          part + (((int64_t)blockIdx.x * Cout + co) * 27 + t) * Cin + g * 16);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) dst[e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
+      for (int e = 0; e < 4; ++e)
+        dst[e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
+    }
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -916,7 +943,7 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
   if (W % 8 == 0 && H % 16 == 0 && cout <= 128 && cin <= cout) {
     // tensor-core path: one persistent CTA per SM (each holds all 512 TMEM columns).
     // Measured faster than the mma.sync kernel where cin <= cout (16 -> 16 at 64^3:
-    // 718 vs 957 us); with more input than output channels the 128-row padding of
+    // 500 vs 957 us); with more input than output channels the 128-row padding of
     // the output channels and one pass per 16 input channels make it slower.
     static int nsm = 0;
     if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
@@ -929,7 +956,7 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
     (void)attr;
     const int ntiles = B * D * (H / 16) * (W / 8);
     const int ncta = std::max(1, std::min(std::min(nsplit, nsm), ntiles));
-    k_conv_wgrad_tc<<<dim3(ncta, cin / 16), 128, WG_SMEM, st0>>>(
+    k_conv_wgrad_tc<<<dim3(ncta, cin / 16), WG_THREADS, WG_SMEM, st0>>>(
         (const bf16*)x, s, cin, (const bf16*)dy, cout, partial);
     const int64_t n = (int64_t)cout * 27 * cin;
     k_sum_partials<<<blocks(n), 256, 0, st0>>>(partial, ncta, n, dw);
