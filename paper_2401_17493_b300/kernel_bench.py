@@ -54,9 +54,13 @@ def main():
         # one Gauss-Newton matvec: sdot_hist, 8 SL steps, accum_hist, spectral, cufft
         "matvec": (lambda: ctx.lib.claire_hessian_matvec(ctx.h, claire._ptr(vt), claire._ptr(w)),
                    None),
+        # one application of the preconditioner (two-level where every n_i % 4 == 0):
+        # fine FFTs, split, the nested CG on the n/2 grid, merge
+        "precond": (lambda: ctx.lib.claire_precondition(ctx.h, claire._ptr(vt), claire._ptr(w),
+                                                        None), None),
     }
     kind = {"sl": "sl_step", "trace": "trace", "grad8": "grad8", "div8": "div8",
-            "matvec": None}
+            "matvec": None, "precond": None}
     res = {}
     for name, (fn, nbytes) in cases.items():
         if args.only and name != args.only:
