@@ -283,6 +283,43 @@ def test_solve_host_equals_device_solve(claire):
     assert sh.matvecs == sd.matvecs
 
 
+@pytest.mark.parametrize("precision,pinned", [(0, True), (1, True), (0, False)])
+def test_solve_host_continuation_equals_device_solve(claire, precision, pinned):
+    """claire_solve_host overlaps its host copies with the solve (the FP32 form uploads
+    m1 on a side stream, accepted steps are copied to pinned host memory as they come):
+    the result is bitwise the device solve's, and the context stays reusable."""
+    shape = (32, 32, 32)
+    m0, m1, _ = _pair(shape, seed=6, kmax=3, disp=2.0)
+    betas = [1e-1, 1e-2, 1e-3]
+    host = (lambda a: torch.from_numpy(a).pin_memory()) if pinned else torch.from_numpy
+    with claire.Context(shape, nt=4, beta_v=1e-1, precision=precision) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        vd, sd = ctx.solve_continuation(betas)
+        vh = host(np.zeros((3,) + shape, dtype=np.float32))
+        vh, sh = ctx.solve_host(host(m0), host(m1), vh, betas)
+        ctx.set_images(dev(m0), dev(m1))
+        vd2, _ = ctx.solve_continuation(betas)
+    assert sh.newton_iters == sd.newton_iters and sd.newton_iters > 1
+    assert sh.matvecs == sd.matvecs
+    assert np.array_equal(vh.numpy(), vd.cpu().numpy())
+    assert np.array_equal(vd2.cpu().numpy(), vd.cpu().numpy())
+
+
+def test_solve_host_from_a_converged_guess_returns_it(claire):
+    """No accepted step: the initial guess comes back unchanged (the result copy is
+    then taken at the end of the call)."""
+    m0, m1, _ = _pair(RAGGED, seed=4, kmax=2, disp=1.5)
+    with claire.Context(RAGGED, nt=4, beta_v=5e-2) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        vd, _ = ctx.solve()
+        v0 = vd.cpu().pin_memory()
+        vh = v0.clone().pin_memory()
+        vh, sh = ctx.solve_host(torch.from_numpy(m0).pin_memory(),
+                                torch.from_numpy(m1).pin_memory(), vh)
+    assert sh.newton_iters == 0
+    assert np.array_equal(vh.numpy(), v0.numpy())
+
+
 @pytest.mark.parametrize("shape", [RAGGED, (32, 32, 32)])
 def test_det_deformation_gradient_matches_oracle(claire, shape):
     _, _, v = _pair(shape, kmax=3, disp=2.0)
