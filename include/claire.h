@@ -337,6 +337,21 @@ claire_status claire_unet_mse(long long V, int C, const float* y, const float* t
 claire_status claire_unet_adam(long long n, float* p, const float* g, float* m, float* v,
                                float lr, float b1, float b2, float eps, int step, void* pb,
                                void* stream);
+/* Bounded waits of the tensor-core kernels.  Every mbarrier wait of the
+ * convolution kernels gives up after 2^22 polls of at most 1 us each; a thread
+ * whose wait ran out writes NaN outputs instead of hanging and is counted in a
+ * device counter.  claire_wait_status synchronises the device, writes the count
+ * since the last call to *timeouts (NULL ok), resets it and returns
+ * CLAIRE_ETIMEOUT if it was nonzero, else CLAIRE_OK.
+ * claire_wait_selftest runs that failure path on purpose: one CTA of 32 threads
+ * polls phase 0 of an mbarrier at most max_polls times (1 <= max_polls <= 2^20,
+ * EINVAL otherwise).  With arrive == 0 nothing arrives: every thread gives up,
+ * 32 timeouts are counted and the call returns CLAIRE_ETIMEOUT.  With arrive != 0
+ * one thread arrives first and the call returns CLAIRE_OK.  No copy or MMA is in
+ * flight in that kernel, so giving up leaves nothing behind and the device stays
+ * usable.  Synchronises the stream. */
+claire_status claire_wait_status(int* timeouts);
+claire_status claire_wait_selftest(int max_polls, int arrive, void* stream);
 /* Spectral resampling of ncomp planar fields [ncomp][n1][n2][n3] onto an
  * m1 x m2 x m3 grid (Sec. 2.5.6, spectral restriction / prolongation): keeps
  * the Fourier modes with |k_i| < min(n_i, m_i) / 2, zero elsewhere.  Even

@@ -28,6 +28,7 @@ EXPORTED = [
     "claire_conv3d_forward", "claire_conv3d_flip_weights", "claire_conv3d_wgrad",
     "claire_unet_op", "claire_unet_bias_grad", "claire_unet_pack", "claire_unet_mse",
     "claire_unet_adam", "claire_resample", "claire_precondition", "claire_beta_search",
+    "claire_wait_status", "claire_wait_selftest",
 ]
 
 
@@ -125,6 +126,8 @@ def load_library(path=LIB_PATH):
         "claire_unet_adam": ([ctypes.c_longlong, P, P, P, P, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, I, P, P], I),
         "claire_resample": ([I, I, I, P, I, I, I, P, I, P], I),
+        "claire_wait_status": ([ctypes.POINTER(I)], I),
+        "claire_wait_selftest": ([I, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -418,3 +421,25 @@ class Context:
                                         "bytes": arr[i].bytes, "ms": arr[i].ms,
                                         "timed_bytes": arr[i].timed_bytes}
                 for i in range(got)}
+
+
+def wait_status():
+    """Threads whose bounded tensor-core wait ran out since the last call (their
+    outputs are NaN); reads and resets the device counter (synchronises)."""
+    L = load_library()
+    n = ctypes.c_int(0)
+    st = L.claire_wait_status(ctypes.byref(n))
+    if st not in (OK, ETIMEOUT):
+        raise ClaireError(st, "claire_wait_status failed")
+    return n.value
+
+
+def wait_selftest(max_polls=1000, arrive=False, stream=None):
+    """Runs the failure path of the bounded waits on purpose (an mbarrier that
+    nothing arrives at unless arrive); returns OK or ETIMEOUT."""
+    L = load_library()
+    st = L.claire_wait_selftest(int(max_polls), 1 if arrive else 0,
+                                ctypes.c_void_p(stream) if stream else None)
+    if st not in (OK, ETIMEOUT):
+        raise ClaireError(st, "claire_wait_selftest failed")
+    return st

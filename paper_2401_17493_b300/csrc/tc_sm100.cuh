@@ -72,6 +72,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
                : "memory");
 }
 
+// One arrival on the mbarrier (the current phase completes once its count is reached).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile(
+      "{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(mbar))
+      : "memory");
+}
+
 // Wait until the phase with the given parity completed.  try_wait suspends the
 // thread for at most the hinted 1000 ns per call (no busy polling); after
 // max_calls calls the wait gives up and returns false (the caller flags the

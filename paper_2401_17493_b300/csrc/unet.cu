@@ -94,6 +94,13 @@ constexpr int CONV_L = 2;                         // stages gathered ahead
 constexpr uint32_t CONV_WAIT = 1u << 22;          // try_wait calls of <= 1 us each
 constexpr int CONV_STAGE_BYTES = 24 * 1024;       // shared memory per stage
 
+// Threads whose bounded tensor-core wait ran out since the last claire_wait_status
+// (their outputs are NaN); read and reset by claire_wait_status.
+__device__ unsigned int g_wait_timeouts = 0;
+__device__ __forceinline__ void note_timeout(bool ok) {
+  if (!ok) atomicAdd(&g_wait_timeouts, 1u);
+}
+
 template <int N, int KC>
 struct ConvSmem {
   static constexpr int A = KC * CONV_M * 32;       // bytes of A per stage
@@ -181,6 +188,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, Vo
     }
   }
   ok &= mbar_wait(&mbar[(nstage - 1) % CONV_S], ((nstage - 1) / CONV_S) & 1, CONV_WAIT);
+  note_timeout(ok);
   tc_fence_after_sync();
 #pragma unroll 1
   for (int c = 0; c < N; c += 16) {
@@ -413,6 +421,7 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __rest
     ok = __syncthreads_and(ok);          // a timed-out wait ends the loop of the whole CTA
   }
   if (it > 0) ok &= mbar_wait(&mbar[(it - 1) & 1], ((it - 1) >> 1) & 1, CONV_WAIT);
+  note_timeout(ok);
   tc_fence_after_sync();
   if (warp < 4) {                                            // TMEM lanes 0..127 = co
     const int co = warp * 32 + (tid & 31);
@@ -787,6 +796,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd_halo(const bf16* __restrict__ 
     last = nstage - 1;
   }
   ok &= mbar_wait(&mbar[last % CONV_S], (last / CONV_S) & 1, CONV_WAIT);
+  note_timeout(ok);
   tc_fence_after_sync();
   const int64_t v = ((int64_t)(b * s.D + z) * s.H + y0 + (tid >> 3)) * s.W + x0 + (tid & 7);
 #pragma unroll 1
@@ -885,6 +895,28 @@ void launch_conv_fwd(dim3 grid, cudaStream_t st, const bf16* X, const Vol& s, in
     case 2: launch_conv_fwd_kc<N, 2>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, Y32); break;
     default: launch_conv_fwd_kc<N, 1>(grid, st, X, s, cin, Wt, bias, cout, relu, Y, Y32); break;
   }
+}
+
+// The failure path of the bounded tensor-core waits, run on purpose: one CTA polls
+// phase 0 of an mbarrier at most max_polls times.  With arrive == 0 nothing
+// arrives and every thread gives up (and counts the timeout); with arrive != 0
+// thread 0 arrives first and every wait succeeds.  No copy or MMA is in flight,
+// so giving up leaves nothing behind.  result = number of threads that gave up.
+__device__ int g_selftest_result = 0;
+__global__ void k_wait_selftest(uint32_t max_polls, int arrive) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int gave_up;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar, 1);
+    gave_up = 0;
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive(&mbar);
+  const bool ok = mbar_wait(&mbar, 0, max_polls);
+  note_timeout(ok);
+  if (!ok) atomicAdd(&gave_up, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) g_selftest_result = gave_up;
 }
 
 }  // namespace
@@ -1050,6 +1082,30 @@ claire_status claire_unet_adam(long long n, float* p, const float* g, float* m, 
   k_adam<<<blocks(n), 256, 0, (cudaStream_t)stream>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2,
                                                       (bf16*)pb);
   return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
+}
+
+claire_status claire_wait_status(int* timeouts) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return CLAIRE_ECUDA;
+  unsigned int n = 0;
+  const unsigned int zero = 0;
+  if (cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof n) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof zero) != cudaSuccess)
+    return CLAIRE_ECUDA;
+  if (timeouts) *timeouts = (int)n;
+  return n ? CLAIRE_ETIMEOUT : CLAIRE_OK;
+}
+
+claire_status claire_wait_selftest(int max_polls, int arrive, void* stream) {
+  if (max_polls < 1 || max_polls > (1 << 20)) return CLAIRE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_wait_selftest<<<1, 32, 0, st>>>((uint32_t)max_polls, arrive);
+  int gave_up = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyFromSymbolAsync(&gave_up, g_selftest_result, sizeof gave_up, 0,
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return CLAIRE_ECUDA;
+  return gave_up ? CLAIRE_ETIMEOUT : CLAIRE_OK;
 }
 
 claire_status claire_resample(int n1, int n2, int n3, const float* in, int m1, int m2, int m3,

@@ -59,6 +59,9 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert h.value is None
     assert lib.claire_destroy(None) == claire.OK
     assert lib.claire_last_error(None) == b"null context"
+    # a wait budget outside 1 .. 2^20 polls is rejected before any launch
+    assert lib.claire_wait_selftest(0, 0, None) == claire.EINVAL
+    assert lib.claire_wait_selftest((1 << 20) + 1, 1, None) == claire.EINVAL
     o = claire.Options()
     assert lib.claire_default_options(ctypes.byref(o)) == claire.OK
     assert abs(o.eps_opt - 5e-2) < 1e-15 and o.max_pcg == 100 and o.hessian == 0
