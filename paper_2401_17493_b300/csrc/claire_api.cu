@@ -15,6 +15,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/claire.h"
 #include "internal.h"
 
@@ -180,6 +182,15 @@ struct Enter {
 };
 #define ENTER(c) Enter enter_guard_(c)
 
+// NVTX range of one solver phase (shown by profilers that record NVTX, e.g. ncu
+// --nvtx; without such a tool attached the calls return at once).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // ---------------------------------------------------------------- reductions
 
 claire_status reduce(claire_ctx* c, int64_t n, const float* a, const float* b, int mode,
@@ -295,6 +306,7 @@ claire_status fp32_histories(claire_ctx* c) {
 
 // m^0 = m0, m^{j+1}(x) = m^j(x + d_f(x))  (eq. transport, homogeneous SL steps)
 claire_status state_solve(claire_ctx* c, const float* d) {
+  NvtxRange nvtx_("claire.state_solve");
   const int64_t N = N_of(c);
   if (!mixed(c)) TRY(fp32_histories(c));
   if (mixed(c)) {                                  // FP16 history of sig_m m
@@ -364,6 +376,7 @@ claire_status objective(claire_ctx* c, const float* v, double* J) {
 // Adjoint solve (eq. adjoint) backward from lam(1) = m1 - m(1), then
 // g = beta_v L v + [I - c P_par] sum_j w_j lam^j grad m^j  (eq. rgrad).
 claire_status adjoint_and_gradient(claire_ctx* c) {
+  NvtxRange nvtx_("claire.adjoint_gradient");
   const int64_t N = N_of(c);
   const Grid& g = c->g;
   if (c->lv_spectrum) {                            // L v of the point objective() evaluated
@@ -425,6 +438,7 @@ claire_status rebeta(claire_ctx* c) {
 
 // Full evaluation at c->v: trace, state, J, adjoint, g (Algorithm 1, lines 3-6).
 claire_status evaluate(claire_ctx* c) {
+  NvtxRange nvtx_("claire.evaluate");
   c->have_eval = false;
   launch_trace(c->g, c->v, c->df, nullptr, ht_of(c), c->st);
   TRY(check_launch(c, "trace"));
@@ -443,6 +457,7 @@ claire_status evaluate(claire_ctx* c) {
 claire_status matvec_transport(claire_ctx* c, const float* vt);
 
 claire_status matvec(claire_ctx* c, const float* vt, float* Hvt) {
+  NvtxRange nvtx_("claire.matvec");
   if (!c->have_eval)
     return fail(c, CLAIRE_EORDER, "hessian_matvec needs a prior objective_gradient");
   const int64_t N = N_of(c);
@@ -742,6 +757,7 @@ claire_status tl_cg_graph(claire_ctx* c) {
 }
 
 claire_status tl_precondition(claire_ctx* c, const float* r, float* z, float* Lz, int rz_slot) {
+  NvtxRange nvtx_("claire.two_level_precondition");
   TRY(tl_setup(c));
   if (!c->tl_image) return fail(c, CLAIRE_EORDER, "two-level preconditioner has no image");
   const Grid& g = c->g;
@@ -921,6 +937,8 @@ claire_status pcg_start(claire_ctx* c);
 claire_status pcg_part(claire_ctx* c, int which, int cur, int nxt) {
   // with the two-level preconditioner parts S and B hold the nested CG as a
   // conditional while node; if that capture is refused, they run launch by launch
+  NvtxRange nvtx_(which == 0 ? "claire.pcg.matvec" : which == 1 ? "claire.pcg.precondition"
+                                                    : "claire.pcg.start");
   auto run = [&]() {
     return which == 0 ? pcg_part_a(c, cur) : which == 1 ? pcg_part_b(c, cur, nxt)
                                                         : pcg_start(c);
@@ -994,6 +1012,7 @@ claire_status pcg_start(claire_ctx* c) {
 }
 
 claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
+  NvtxRange nvtx_("claire.pcg");
   const int64_t N = N_of(c);
   const int64_t n3 = 3 * N;
   *curv = CLAIRE_OK;
@@ -1043,6 +1062,7 @@ claire_status pcg(claire_ctx* c, double tol, Counters& k, claire_status* curv) {
 // Armijo backtracking (reading C-9) on J(v + gamma vt); on success the state
 // history, departure points and L v belong to the accepted point.
 claire_status armijo(claire_ctx* c, Counters& k, double* gamma_out, bool* ok) {
+  NvtxRange nvtx_("claire.armijo");
   const int64_t n3 = 3 * N_of(c);
   const double h3 = (double)c->g.h1 * c->g.h2 * c->g.h3;
   double gv = 0.0;
@@ -1136,6 +1156,7 @@ claire_status autotune(claire_ctx* c) {
 claire_status detf_stats(claire_ctx* c, const float* v, double* mmm, float* det_out);
 
 claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_stats* out) {
+  NvtxRange nvtx_("claire.gauss_newton");
   const int64_t n3 = 3 * N_of(c);
   double vmax = 0.0;
   TRY(absmax3(c, c->v, &vmax));
@@ -1168,6 +1189,7 @@ claire_status gauss_newton(claire_ctx* c, double gnorm0, Counters& k, claire_sta
   int iters = 0;
   while (iters < c->opt.max_newton) {
     if (!c->opt.fixed_iters && (gn <= c->opt.eps_opt * gnorm0 || gn <= 1e-6)) break;
+    NvtxRange nvtx_it("claire.newton_iteration");
     const double ratio = gn / gnorm0;
     const double eta = std::fmin(0.5, c->opt.forcing == 0 ? std::sqrt(ratio) : ratio);
     double gg = 0.0;
@@ -1558,6 +1580,7 @@ claire_status claire_hessian_matvec(claire_ctx* c, const float* vt, float* Hvt) 
 // iterate already held in c->v.
 static claire_status solve_levels(claire_ctx* c, const double* betas, int nlev, const float* v_in,
                                   float* v_out, claire_stats* st) {
+  NvtxRange nvtx_("claire.solve");
   if (!c || nlev < 1) return CLAIRE_EINVAL;
   ENTER(c);
   for (int i = 0; i < nlev; ++i)
