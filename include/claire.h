@@ -279,6 +279,18 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
  * nothing has been evaluated yet.  The chosen shapes are returned (NULL ok). */
 claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
 
+/* ---- gathers outside the staged brick ---------------------------------------
+ * The SL steps stage a brick of the source field around each tile (a halo of 3
+ * nodes along x1 and x2, 4 along x3) and interpolate from shared memory; a node
+ * whose 4 x 4 x 4 taps leave the brick (floor of the displacement outside
+ * [-2, 1] along x1 or x2, [-3, 2] along x3) takes the global-memory gather
+ * instead, with the same result.  *fwd / *bwd = the number of such nodes for
+ * the forward (state, incremental state) and backward (adjoint, incremental
+ * adjoint) departure points of the last evaluation: every SL step in that
+ * direction gathers those nodes from global memory.  EORDER before an
+ * evaluation.  Synchronises the context's stream. */
+claire_status claire_far_nodes(claire_ctx* ctx, long long* fwd, long long* bwd);
+
 /* ---- learned warm start: 3D U-Net kernels --------------------------------------
  * Not part of the paper: a small 3D U-Net predicts an initial velocity from
  * the image pair on a 64^3 grid.  Activations are channels-last BF16 [V][C]

@@ -28,7 +28,7 @@ EXPORTED = [
     "claire_conv3d_forward", "claire_conv3d_flip_weights", "claire_conv3d_wgrad",
     "claire_unet_op", "claire_unet_bias_grad", "claire_unet_pack", "claire_unet_mse",
     "claire_unet_adam", "claire_resample", "claire_precondition", "claire_beta_search",
-    "claire_wait_status", "claire_wait_selftest",
+    "claire_wait_status", "claire_wait_selftest", "claire_far_nodes",
 ]
 
 
@@ -128,6 +128,8 @@ def load_library(path=LIB_PATH):
         "claire_resample": ([I, I, I, P, I, I, I, P, I, P], I),
         "claire_wait_status": ([ctypes.POINTER(I)], I),
         "claire_wait_selftest": ([I, I, P], I),
+        "claire_far_nodes": ([P, ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -406,6 +408,13 @@ class Context:
         return a.value, b.value
 
     # -- launch accounting
+    def far_nodes(self):
+        """(forward, backward): nodes whose departure points of the last evaluation
+        leave the staged SL brick (interpolated by the global-memory gather)."""
+        f, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        self._check(self.lib.claire_far_nodes(self.h, ctypes.byref(f), ctypes.byref(b)))
+        return f.value, b.value
+
     def profile_reset(self, timing=False):
         self._check(self.lib.claire_profile_reset(self.h, 1 if timing else 0))
 

@@ -46,6 +46,7 @@ struct claire_ctx {
   float* vbest = nullptr;       // velocity of the last admissible beta (claire_beta_search)
   double* slots = nullptr;      // device FP64 scalars of PCG (see pcg())
   int* dflag = nullptr;         // device flag: negative curvature / non-finite PCG scalar
+  unsigned long long* far = nullptr;  // count of claire_far_nodes
   double* hslots = nullptr;     // pinned host mirror of slots + flag
   int partial_blocks = 0;
   // mixed precision (options.precision = 1): FP16 histories, allocated on first use
@@ -1415,6 +1416,8 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
       c->dres = c->partial + pb;
       c->slots = c->dres + 8;
       c->dflag = (int*)(c->slots + NSLOTS);
+      c->far = (unsigned long long*)(c->slots + NSLOTS + 2);
+      if (cudaMemset(c->far, 0, sizeof *c->far) != cudaSuccess) s = CLAIRE_ECUDA;
       c->bytes += (size_t)(pb + 8 + NSLOTS + 4) * sizeof(double);
     }
   }
@@ -1909,6 +1912,24 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
     for (int i = 0; i < npairs; ++i)
       if (res[i] != CLAIRE_OK) worst = res[i];
   return worst;
+}
+
+claire_status claire_far_nodes(claire_ctx* c, long long* fwd, long long* bwd) {
+  if (!c || !fwd || !bwd) return CLAIRE_EINVAL;
+  ENTER(c);
+  if (!c->have_eval) return fail(c, CLAIRE_EORDER, "far_nodes needs an evaluated velocity");
+  long long* res[2] = {fwd, bwd};
+  const float* d[2] = {c->df, c->db};
+  for (int k = 0; k < 2; ++k) {
+    unsigned long long n = 0;
+    CUDA_TRY(c, cudaMemsetAsync(c->far, 0, sizeof n, c->st));
+    launch_count_far(c->g, d[k], c->far, c->st);
+    TRY(check_launch(c, "far nodes"));
+    CUDA_TRY(c, cudaMemcpyAsync(&n, c->far, sizeof n, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    *res[k] = (long long)n;
+  }
+  return CLAIRE_OK;
 }
 
 claire_status claire_autotune(claire_ctx* c, int* sl_t1, int* march_t1) {

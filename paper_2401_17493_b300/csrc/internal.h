@@ -62,6 +62,8 @@ struct ProfileRange {
 };
 
 void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht, cudaStream_t st);
+// adds to *out the nodes whose departure points d leave the SL brick (global gather)
+void launch_count_far(const Grid& g, const float* d, unsigned long long* out, cudaStream_t st);
 void launch_sl(const Grid& g, const float* u, const float* d, const float* scale, float sigma,
                const float* aux, float beta, float* out, cudaStream_t st);
 void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float ht, float* c,

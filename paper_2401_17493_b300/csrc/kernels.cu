@@ -152,6 +152,30 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl(Grid g, const float* __
   }
 }
 
+// Nodes whose departure point d (grid units) puts a tap outside the staged brick,
+// i.e. the nodes an SL step with these departure points interpolates with the
+// global-memory gather (the predicate of k_sl); block counts added into *out.
+__global__ void __launch_bounds__(256) k_count_far(int64_t N, const float* __restrict__ d,
+                                                   unsigned long long* __restrict__ out) {
+  unsigned cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    NodeTaps t;
+    node_taps(d[i], d[N + i], d[2 * N + i], t);
+    cnt += !taps_in_brick(t);
+  }
+  __shared__ unsigned warp_cnt[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < 8; ++w) b += warp_cnt[w];
+    if (b) atomicAdd(out, b);
+  }
+}
+
 // ---------------------------------------------------------------- FD8
 
 __global__ void __launch_bounds__(256) k_grad8(Grid g, const float* __restrict__ u,
@@ -747,6 +771,10 @@ void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float
   const int t1 = tuned_sl_t1();
   k_sl<1><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
       g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1);
+}
+void launch_count_far(const Grid& g, const float* d, unsigned long long* out,
+                      cudaStream_t st) {
+  k_count_far<<<vec_blocks(g.N), 256, 0, st>>>(g.N, d, out);
 }
 void launch_grad8(const Grid& g, const float* u, float* gu, cudaStream_t st) {
   ProfileRange pr(K_GRAD8, (double)g.N * 16, st);

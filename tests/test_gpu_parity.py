@@ -99,6 +99,34 @@ def test_interpolation_wraps_large_displacements(claire):
     assert rel(host(out), OI.interp(_f64(u), base + _f64(d))) < 1e-5
 
 
+def test_far_node_count_matches_the_departure_points(claire):
+    """claire_far_nodes counts the nodes whose departure points leave the staged SL
+    brick (floor of d outside [-2, 1] on x1 and x2, [-3, 2] on x3): exactly the
+    count of the trace's own departure points, zero for small displacements."""
+    m0, m1, _ = _pair(RAGGED, seed=3)
+
+    def outside(d):
+        p = np.floor(d.cpu().numpy())
+        return int(((p[0] < -2) | (p[0] > 1) | (p[1] < -2) | (p[1] > 1) |
+                    (p[2] < -3) | (p[2] > 2)).sum())
+
+    for disp in (0.5, 12.0):                  # voxels per unit time; n_t = 4 steps
+        v = synth.bandlimited_velocity(RAGGED, 3, disp, 21).astype(np.float32)
+        with claire.Context(RAGGED, nt=4) as ctx:
+            ctx.set_images(dev(m0), dev(m1))
+            with pytest.raises(claire.ClaireError) as e:
+                ctx.far_nodes()
+            assert e.value.status == claire.EORDER
+            ctx.objective_gradient(dev(v))
+            fwd, bwd = ctx.far_nodes()
+            df, db = ctx.trace(dev(v))
+        assert (fwd, bwd) == (outside(df), outside(db))
+        if disp < 1.0:
+            assert fwd == 0 and bwd == 0
+        else:
+            assert fwd > 0 and bwd > 0
+
+
 @pytest.mark.parametrize("shape", [RAGGED, CUBE])
 def test_fd8_gradient_and_divergence_match_oracle(claire, shape):
     u = synth.smooth_field(shape, 5, 3).astype(np.float32)
