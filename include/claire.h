@@ -314,9 +314,12 @@ claire_status claire_conv3d_flip_weights(const void* w, int cout, int cin, void*
 /* Weight gradient dw[cout][27][cin] (FP32) = sum_v dy[v][n] x[nbr_t(v)][c], as at
  * most nsplit partial sums written to partial (room for nsplit x cout x 27 x cin
  * floats) and added in a fixed order.  cin in {16, 32, 48, 64, 96, 128, 192}.
- * With W % 8 == 0, H % 16 == 0 and cin <= cout <= 128 it runs on the tcgen05
- * tensor cores (min(nsplit, SMs, 8 x 16-voxel tiles) persistent CTAs, one partial
- * each), otherwise on mma.sync over voxel chunks of at least 4096 voxels. */
+ * On the tcgen05 tensor cores, with min(nsplit, SMs, tiles) persistent CTAs (one
+ * partial each): with the output channels as MMA rows where W % 8 == 0,
+ * H % 16 == 0 and cin <= cout <= 128 (8 x 16-voxel tiles); else with the input
+ * channels as MMA rows where W % 8 == 0, H % 8 == 0 and cout <= 32 or
+ * H % 16 != 0 (8 x 8-voxel tiles).  Otherwise on mma.sync over voxel chunks of
+ * at least 4096 voxels. */
 claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int cin,
                                   const void* dy, int cout, float* partial, int nsplit,
                                   float* dw, void* stream);

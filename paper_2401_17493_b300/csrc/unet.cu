@@ -445,6 +445,156 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __rest
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// Weight gradient on the tensor cores in the transposed orientation, for the
+// layers the kernel above does not take (more input than output channels, or
+// H % 16 != 0 such as the 8^3 bottleneck); needs W % 8 == 0 and H % 8 == 0:
+//   D[ci][(t, co)] += A_t[ci][v] B[co][v]
+// with M = 128 input channels (blockIdx.y / (cout / 16) selects the block of 128,
+// rows >= cin unused), N = 16 output channels (blockIdx.y % (cout / 16)), K =
+// voxels.  A persistent CTA walks 8 x 8-voxel tiles of one (sample, z) in three
+// stages per tile, one per x shift dx: a stage holds the input neighbourhood of
+// that shift transposed, XT[z'(3)][y'(10)][ci(128)][x(8)] (every tap's A operand
+// starts on a 16-byte row), and dY of the tile transposed, [y(8)][co(16)][x(8)]
+// (the B operand); one thread issues the 9 taps of the shift x 4 MMAs (K = 16:
+// two y rows each) while the CTA stages the next stage into the other of two
+// buffers.  All 27 taps accumulate in 432 TMEM columns.  The CTA's partial dW goes
+// to part[blockIdx.x]; every wait is bounded (a timed-out one makes it NaN).
+constexpr int WT_XP = 128 * 16 + 16;                      // 2064 bytes per (z', y') block
+constexpr int WT_XT = 3 * 10 * WT_XP;                     // 61920
+constexpr int WT_BP = 16 * 16 + 16;                       // 272 bytes per y row of B
+constexpr int WT_B = 8 * WT_BP;                           // 2176
+constexpr int WT_BUF = WT_XT + WT_B;                      // one stage's operands
+constexpr int WT_SMEM = 2 * WT_BUF;
+static_assert(WT_BUF % 16 == 0, "stage buffers on 16-byte boundaries");
+static_assert(WT_SMEM > 114 * 1024 && WT_SMEM <= 227 * 1024, "one CTA per SM");
+__global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc_t(const bf16* __restrict__ X,
+                                                                Vol s, int Cin,
+                                                                const bf16* __restrict__ dY,
+                                                                int Cout,
+                                                                float* __restrict__ part) {
+  extern __shared__ __align__(128) uint8_t wt_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ncg = Cout / 16;
+  const int g = blockIdx.y % ncg;                            // output channels 16 g ..
+  const int m0 = (blockIdx.y / ncg) * 128;                   // input channels m0 ..
+  const int cm = min(128, Cin - m0);                         // real rows of A
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  for (int i = tid; i < WT_SMEM / 16; i += WG_THREADS)
+    reinterpret_cast<uint4*>(wt_smem)[i] = make_uint4(0, 0, 0, 0);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = umma_idesc_bf16(CONV_M, 16);
+  const int xb = s.W / 8, yb = s.H / 8;
+  const int ntiles = s.B * s.D * yb * xb;
+  const int nloc = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / gridDim.x + 1 : 0;
+  const int nst = 3 * nloc;                                  // stages: (local tile, dx)
+  // the operands of stage st into buffer buf
+  auto stage = [&](int st, int buf) {
+    uint8_t* XT = wt_smem + buf * WT_BUF;
+    uint8_t* Bo = XT + WT_XT;
+    int q = (int)blockIdx.x + (st / 3) * (int)gridDim.x;
+    const int dx = st % 3;
+    const int x0 = (q % xb) * 8;
+    q /= xb;
+    const int y0 = (q % yb) * 8;
+    q /= yb;
+    const int z = q % s.D, b = q / s.D;
+    // B[y][co][x] = dY[(x0 + x, y0 + y)][16 g + co]
+    if (tid < 128) {
+      const int v = tid & 63, c8 = tid >> 6;
+      const int y = v >> 3, x = v & 7;
+      const int64_t vv = ((int64_t)(b * s.D + z) * s.H + y0 + y) * s.W + x0 + x;
+      const uint4 d = *reinterpret_cast<const uint4*>(dY + vv * Cout + g * 16 + c8 * 8);
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        *reinterpret_cast<uint16_t*>(Bo + y * WT_BP + (c8 * 8 + e) * 16 + x * 2) = h[e];
+    }
+    // XT[zp][yp][ci][x] = X[(x0 + x + dx - 1, y0 + yp - 1, z + zp - 1)][m0 + ci]; a warp's
+    // lanes take 8 x by 4 consecutive (zp, yp) blocks (block pitch 2064 bytes: the
+    // four blocks start in different banks)
+    const int nch = cm / 8;
+#pragma unroll 4
+    for (int i = tid; i < 256 * nch; i += WG_THREADS) {
+      const int x = i & 7, c8 = (i >> 8);
+      const int blk = ((i >> 5) & 7) * 4 + ((i >> 3) & 3);
+      if (blk >= 30) continue;
+      const int yp = blk % 10, zp = blk / 10;
+      int xx = x0 + x + dx - 1, yy = y0 + yp - 1, zz = z + zp - 1;
+      xx = xx < 0 ? xx + s.W : (xx >= s.W ? xx - s.W : xx);
+      yy = yy < 0 ? yy + s.H : (yy >= s.H ? yy - s.H : yy);
+      zz = zz < 0 ? zz + s.D : (zz >= s.D ? zz - s.D : zz);
+      const int64_t vv = ((int64_t)(b * s.D + zz) * s.H + yy) * s.W + xx;
+      const uint4 d = *reinterpret_cast<const uint4*>(X + vv * Cin + m0 + c8 * 8);
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
+      uint8_t* row = XT + blk * WT_XP + c8 * 8 * 16 + x * 2;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) *reinterpret_cast<uint16_t*>(row + e * 16) = h[e];
+    }
+    fence_proxy_async_smem();
+  };
+  bool ok = true;
+  if (nst > 0) stage(0, 0);
+  ok = __syncthreads_and(ok);
+  int st = 0;
+  for (; st < nst && ok; ++st) {
+    const int buf = st & 1;
+    if (tid == 0) {
+      tc_fence_after_sync();
+      const uint8_t* XT = wt_smem + buf * WT_BUF;
+      const uint8_t* Bo = XT + WT_XT;
+      const int dx = st % 3, lt = st / 3;
+      for (int dz = 0; dz < 3; ++dz)
+        for (int dy = 0; dy < 3; ++dy) {
+          const int t = dz * 9 + dy * 3 + dx;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            umma_bf16(tmem + (uint32_t)(t * 16),
+                      umma_smem_desc(XT + (dz * 10 + 2 * j + dy) * WT_XP, WT_XP, 128),
+                      umma_smem_desc(Bo + j * 2 * WT_BP, WT_BP, 128), idesc,
+                      (lt > 0 || j > 0) ? 1u : 0u);
+        }
+      umma_commit(&mbar[buf]);
+    }
+    if (st + 1 < nst) {
+      // the other buffer was read by the MMAs of stage st - 1
+      if (st >= 1) ok = mbar_wait(&mbar[buf ^ 1], ((st - 1) >> 1) & 1, CONV_WAIT);
+      if (ok) stage(st + 1, buf ^ 1);
+    }
+    ok = __syncthreads_and(ok);          // a timed-out wait ends the loop of the whole CTA
+  }
+  if (st > 0) ok &= mbar_wait(&mbar[(st - 1) & 1], ((st - 1) >> 1) & 1, CONV_WAIT);
+  note_timeout(ok);
+  tc_fence_after_sync();
+  if (warp < 4) {                                            // TMEM lanes 0..127 = ci
+    const int ci = m0 + warp * 32 + (tid & 31);
+#pragma unroll 1
+    for (int t = 0; t < 27; ++t) {
+      float y[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 16), y);
+      if (ci >= Cin || warp * 32 + (tid & 31) >= cm) continue;
+#pragma unroll
+      for (int n = 0; n < 16; ++n)
+        part[(((int64_t)blockIdx.x * Cout + g * 16 + n) * 27 + t) * Cin + ci] =
+            !ok ? __int_as_float(0x7fc00000) : (st > 0 ? y[n] : 0.f);
+    }
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 __global__ void k_sum_partials(const float* __restrict__ part, int nsplit, int64_t n,
                                float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -989,6 +1139,30 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
     const int ntiles = B * D * (H / 16) * (W / 8);
     const int ncta = std::max(1, std::min(std::min(nsplit, nsm), ntiles));
     k_conv_wgrad_tc<<<dim3(ncta, cin / 16), WG_THREADS, WG_SMEM, st0>>>(
+        (const bf16*)x, s, cin, (const bf16*)dy, cout, partial);
+    const int64_t n = (int64_t)cout * 27 * cin;
+    k_sum_partials<<<blocks(n), 256, 0, st0>>>(partial, ncta, n, dw);
+    return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
+  }
+  if (W % 8 == 0 && H % 8 == 0 && (cout <= 32 || H % 16 != 0)) {
+    // tensor-core path, transposed: input channels as the 128 MMA rows (one grid row
+    // per block of 128 input channels and 16 output channels), one persistent CTA per SM.
+    // Each grid row stages the input neighbourhood again, so with 64 or more output
+    // channels on H % 16 == 0 grids (192 -> 64 at 16^3: 235 vs 194 us) mma.sync stays
+    static int nsm_t = 0;
+    if (nsm_t == 0 &&
+        cudaDeviceGetAttribute(&nsm_t, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
+      return CLAIRE_ECUDA;
+    static const bool attr_t = [] {
+      cudaFuncSetAttribute(k_conv_wgrad_tc_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           WT_SMEM);
+      return true;
+    }();
+    (void)attr_t;
+    const int ntiles = B * D * (H / 8) * (W / 8);
+    const int ncta = std::max(1, std::min(std::min(nsplit, nsm_t), ntiles));
+    const int nmt = (cin + 127) / 128;
+    k_conv_wgrad_tc_t<<<dim3(ncta, nmt * (cout / 16)), WG_THREADS, WT_SMEM, st0>>>(
         (const bf16*)x, s, cin, (const bf16*)dy, cout, partial);
     const int64_t n = (int64_t)cout * 27 * cin;
     k_sum_partials<<<blocks(n), 256, 0, st0>>>(partial, ncta, n, dw);

@@ -52,12 +52,19 @@ def _to_cl(x):
 
 # shapes with H % 16 == 0 and W % 8 == 0 take the halo-tile forward kernel (one
 # chunk group, weights resident or streamed; several groups for 96 input channels
-# and, in the data gradient, 80 and 128), the first three the per-tap gather kernel
+# and, in the data gradient, 80 and 128), the first three the per-tap gather kernel.
+# Weight gradient: tcgen05 with the output channels as MMA rows where W % 8 == 0,
+# H % 16 == 0 and cin <= cout <= 128; else, with W % 8 == 0, H % 8 == 0 and
+# cout <= 32 or H % 16 != 0, tcgen05 with the input channels as MMA rows (48 -> 16,
+# 64 -> 32, 96 -> 32, the 8^3 and H = 8 shapes, two row blocks for 192 -> 32);
+# else mma.sync (192 -> 64)
 @pytest.mark.parametrize("cin,cout,shape", [(16, 16, (8, 6, 10)), (48, 32, (6, 6, 6)),
                                             (32, 64, (4, 8, 4)), (16, 16, (4, 16, 8)),
                                             (48, 16, (3, 16, 16)), (64, 32, (2, 32, 8)),
                                             (32, 128, (5, 16, 24)), (16, 80, (2, 16, 8)),
-                                            (96, 32, (3, 16, 8))])
+                                            (96, 32, (3, 16, 8)), (48, 16, (2, 8, 16)),
+                                            (128, 128, (8, 8, 8)), (64, 128, (4, 8, 8)),
+                                            (192, 32, (2, 16, 8)), (192, 64, (2, 16, 8))])
 def test_conv_forward_dgrad_wgrad_match_oracle(lib, cin, cout, shape):
     rng = np.random.default_rng(cin + cout)
     x = _bf(rng.standard_normal((cin,) + shape))
