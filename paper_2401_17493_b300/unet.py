@@ -6,8 +6,8 @@ accumulation, 3x3x3 periodic convolutions) maps the image pair (m0, m1),
 spectrally restricted to 64^3, to a velocity on 64^3 that is spectrally
 prolonged to the registration grid and used as the solver's initial guess.
 The plain zero-initialised solve is both the fallback (taken when the
-prediction raises the objective) and the judge (same relative-gradient
-tolerance, denominator ||g(v = 0)||_inf for both).
+prediction raises the objective) and the accuracy reference (same
+relative-gradient tolerance, denominator ||g(v = 0)||_inf for both).
 
 Every layer runs in the library's kernels (claire_conv3d_forward / wgrad /
 flip_weights, claire_unet_op / bias_grad / pack / mse / adam,
