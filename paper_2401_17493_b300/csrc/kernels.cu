@@ -18,6 +18,7 @@
 #include <atomic>
 #include <mutex>
 
+#include "device_setup.h"
 #include "internal.h"
 #include "reduce.cuh"
 #include "sl_brick.cuh"
@@ -722,16 +723,11 @@ ProfileRange::~ProfileRange() {
 
 // ---------------------------------------------------------------- launchers
 
-static std::atomic<int> g_num_sms{0};
 static int vec_blocks(int64_t n) {
-  if (g_num_sms.load() == 0) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_num_sms.store(sms > 0 ? sms : 148);
-  }
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 148;
   int64_t want = (n + 255) / 256;
-  int64_t cap = (int64_t)g_num_sms * 16;
+  int64_t cap = (int64_t)sms * 16;
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
@@ -740,8 +736,8 @@ int tuned_sl_t1() { return tl_tune ? tl_tune->sl_t1 : TB1; }
 int tuned_march_t1() { return tl_tune ? tl_tune->march_t1 : MT1; }
 
 static void brick_attributes() {
-  static std::once_flag once;
-  std::call_once(once, [] {
+  static std::once_flag once[kSetupDevices];
+  once_per_device(once, [] {
     const int mx = brick_floats(16) * (int)sizeof(float);
     cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_sl<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

@@ -18,6 +18,7 @@
 
 #include <mutex>
 
+#include "device_setup.h"
 #include "internal.h"
 #include "reduce.cuh"
 #include "sl_brick.cuh"
@@ -179,8 +180,8 @@ __global__ void __launch_bounds__(256) k_sqdiff_h(int64_t n, const __half* __res
 
 void launch_sl_h(const Grid& g, const __half* u, const float* d, const float* scale,
                  float sigma, const __half* aux, float beta, __half* out, cudaStream_t st) {
-  static std::once_flag once;
-  std::call_once(once, [] {
+  static std::once_flag once[kSetupDevices];
+  once_per_device(once, [] {
     cudaFuncSetAttribute(k_sl_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          brick_floats(16) * (int)sizeof(float));
   });

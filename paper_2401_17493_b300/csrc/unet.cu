@@ -20,6 +20,7 @@
 
 #include "../../include/claire.h"
 #include "common.cuh"
+#include "device_setup.h"
 #include "reduce.cuh"
 #include "tc_sm100.cuh"
 
@@ -987,12 +988,11 @@ void launch_conv_fwd_halo_g(cudaStream_t st, const bf16* X, const Vol& s, int ci
                             const bf16* Wt, const float* bias, int cout, int relu, bf16* Y,
                             float* Y32) {
   constexpr int bytes = HaloSmem<N, G>::bytes;
-  static const bool attr = [] {
+  static std::once_flag once[kSetupDevices];
+  once_per_device(once, [] {
     cudaFuncSetAttribute(k_conv_fwd_halo<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          bytes);
-    return true;
-  }();
-  (void)attr;
+  });
   const dim3 grid(s.B * s.D * (s.H / 16) * (s.W / 8), cout / N);
   k_conv_fwd_halo<N, G><<<grid, 128, bytes, st>>>(X, s, cin, Wt, bias, cout, relu, Y, Y32);
 }
@@ -1017,11 +1017,10 @@ void launch_conv_fwd_kc(dim3 grid, cudaStream_t st, const bf16* X, const Vol& s,
                         const bf16* Wt, const float* bias, int cout, int relu, bf16* Y,
                         float* Y32) {
   constexpr int bytes = ConvSmem<N, KC>::bytes;
-  static const bool attr = [] {
+  static std::once_flag once[kSetupDevices];
+  once_per_device(once, [] {
     cudaFuncSetAttribute(k_conv_fwd<N, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return true;
-  }();
-  (void)attr;
+  });
   k_conv_fwd<N, KC><<<grid, 128, bytes, st>>>(X, s, cin, Wt, bias, cout, relu, Y, Y32);
 }
 
@@ -1129,15 +1128,13 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
     // Measured faster than the mma.sync kernel where cin <= cout (16 -> 16 at 64^3:
     // 500 vs 957 us); with more input than output channels the 128-row padding of
     // the output channels and one pass per 16 input channels make it slower.
-    static int nsm = 0;
-    if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
-      return CLAIRE_ECUDA;
-    static const bool attr = [] {
+    const int nsm = device_sm_count();
+    if (nsm == 0) return CLAIRE_ECUDA;
+    static std::once_flag once[kSetupDevices];
+    once_per_device(once, [] {
       cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            WG_SMEM);
-      return true;
-    }();
-    (void)attr;
+    });
     const int ntiles = B * D * (H / 16) * (W / 8);
     const int ncta = std::max(1, std::min(std::min(nsplit, nsm), ntiles));
     k_conv_wgrad_tc<<<dim3(ncta, cin / 16), WG_THREADS, WG_SMEM, st0>>>(
@@ -1151,16 +1148,13 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
     // per block of 128 input channels and 16 output channels), one persistent CTA per SM.
     // Each grid row stages the input neighbourhood again, so with 64 or more output
     // channels on H % 16 == 0 grids (192 -> 64 at 16^3: 235 vs 194 us) mma.sync stays
-    static int nsm_t = 0;
-    if (nsm_t == 0 &&
-        cudaDeviceGetAttribute(&nsm_t, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
-      return CLAIRE_ECUDA;
-    static const bool attr_t = [] {
+    const int nsm_t = device_sm_count();
+    if (nsm_t == 0) return CLAIRE_ECUDA;
+    static std::once_flag once_t[kSetupDevices];
+    once_per_device(once_t, [] {
       cudaFuncSetAttribute(k_conv_wgrad_tc_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            WT_SMEM);
-      return true;
-    }();
-    (void)attr_t;
+    });
     const int ntiles = B * D * (H / 8) * (W / 8);
     const int ncta = std::max(1, std::min(std::min(nsplit, nsm_t), ntiles));
     const int nmt = (cin + 127) / 128;
