@@ -231,20 +231,21 @@ def run_batch(args, pairs):
 def cpu_oracle_sample(m0, m1, n_full):
     """FP64 oracle continuation solve of the workload restricted to 32^3, scaled by
     the voxel ratio to the full grid (the 256^3 solve takes more iterations, so the
-    scaled figure underestimates the CPU time)."""
+    scaled figure underestimates the CPU time).  Returns (scaled s, measured s,
+    stats, threads used = process CPU time / wall time, rounded, at least 1)."""
     import numpy as np
     from oracle import reduced, solver, spectral
     ns = CPU_SAMPLE_N
     a = spectral.restrict(m0.astype(np.float64), (ns,) * 3)
     b = spectral.restrict(m1.astype(np.float64), (ns,) * 3)
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     prob = reduced.Problem(a, b, nt=NT, beta_v=BETAS[0])
     _, st, _ = solver.continuation(prob, BETAS, solver.Options(
         eps_opt=EPS_OPT, max_pcg=MAX_PCG, precond="two_level" if PRECOND else "spectral",
         max_inner=MAX_INNER))
-    dt = time.perf_counter() - t0
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
     scale = (n_full / ns) ** 3
-    return dt * scale, dt, st
+    return dt * scale, dt, st, max(1, int(round(cpu / dt)))
 
 
 def run_reference(args, world, rank):
@@ -255,16 +256,17 @@ def run_reference(args, world, rank):
     m0, m1 = workload(n)
     for _ in range(args.warmup):
         cpu_oracle_sample(m0, m1, n)
-    vals, raw = [], []
+    vals, raw, used = [], [], []
     for _ in range(args.steps):
-        v, dt, st = cpu_oracle_sample(m0, m1, n)
+        v, dt, st, th = cpu_oracle_sample(m0, m1, n)
         vals.append(v)
         raw.append(dt)
+        used.append(th)
     value = float(np.mean(vals))
-    cores = os.cpu_count()
+    cores = max(used)
     sample = (f"oracle FP64 continuation solve of the {CPU_SAMPLE_N}^3 spectral restriction of "
               f"the {n}^3 pair ({np.mean(raw):.2f} s per solve), scaled x{(n // CPU_SAMPLE_N) ** 3}"
-              " by voxel count")
+              f" by voxel count; {cores} thread(s) busy of {os.cpu_count()} logical CPUs")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -442,10 +444,11 @@ def run_claire(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, raw, _ = cpu_oracle_sample(m0, m1, n)
-        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+        est, raw, _, used = cpu_oracle_sample(m0, m1, n)
+        cpu = {"value": est, "unit": "s", "cores": used, "kind": "oracle",
                "sample": f"oracle FP64 continuation solve of the {CPU_SAMPLE_N}^3 restriction "
-                         f"({raw:.2f} s), scaled x{(n // CPU_SAMPLE_N) ** 3} by voxel count"}
+                         f"({raw:.2f} s), scaled x{(n // CPU_SAMPLE_N) ** 3} by voxel count; "
+                         f"{used} thread(s) busy of {os.cpu_count()} logical CPUs"}
 
     st0 = stats[-1]
     line = {
