@@ -272,12 +272,26 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
                                  int max_threads);
 
 /* ---- autotuner -------------------------------------------------------------
- * Times the compiled tile shapes of the SL gather (brick depth along x1: 4, 8
- * or 16 nodes) and of the FD8 history kernels (8, 16, 32 or 64 planes per
+ * Times the compiled tile shapes of the SL gather (both gather variants, brick
+ * depth along x1: 4, 8 or 16 nodes) and of the FD8 history kernels (8, 16, 32 or 64 planes per
  * CTA) on this context's grid and buffers and keeps the fastest for all later
  * calls on the context.  Evaluates J and g at the context's current v first if
  * nothing has been evaluated yet.  The chosen shapes are returned (NULL ok). */
 claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
+
+/* Sets the tile shapes by hand (kept by options.autotune; drops captured graphs):
+ *  sl_window  0: SL gathers with 64 shared loads per node (default);
+ *             1: a per-lane register window of four x1 tap planes (16 shared
+ *             loads per node whose displacement floor equals the lane's
+ *             reference floor; the other nodes are gathered afterwards by the
+ *             whole CTA from the brick).  Both give bitwise the same values;
+ *  sl_t1      4, 8 or 16 nodes per thread along x1 (default 8);
+ *  march_t1   8, 16, 32 or 64 planes per CTA of the FD8 history kernels (default 32).
+ * EINVAL for any other value.  claire_get_tuning reads the current shapes (the
+ * autotuner's choice after claire_autotune); NULL outputs are skipped. */
+claire_status claire_set_tuning(claire_ctx* ctx, int sl_window, int sl_t1, int march_t1);
+claire_status claire_get_tuning(const claire_ctx* ctx, int* sl_window, int* sl_t1,
+                                int* march_t1);
 
 /* ---- gathers outside the staged brick ---------------------------------------
  * The SL steps stage a brick of the source field around each tile (a halo of 3

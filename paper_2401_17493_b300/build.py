@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libclaire.so")
 SOURCES = ["kernels.cu", "mixed.cu", "claire_api.cu", "noalloc.cu", "unet.cu", "precond.cu"]
-HEADERS = ["common.cuh", "internal.h", "sl_brick.cuh", "fd8_march.cuh", "reduce.cuh",
+HEADERS = ["common.cuh", "internal.h", "sl_brick.cuh", "sl_window.cuh", "fd8_march.cuh",
+           "reduce.cuh",
            "device_setup.h", "tc_sm100.cuh"]
 
 NVCC_FLAGS = [

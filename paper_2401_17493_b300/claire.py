@@ -28,7 +28,8 @@ EXPORTED = [
     "claire_conv3d_forward", "claire_conv3d_flip_weights", "claire_conv3d_wgrad",
     "claire_unet_op", "claire_unet_bias_grad", "claire_unet_pack", "claire_unet_mse",
     "claire_unet_adam", "claire_resample", "claire_precondition", "claire_beta_search",
-    "claire_wait_status", "claire_wait_selftest", "claire_far_nodes",
+    "claire_wait_status", "claire_wait_selftest", "claire_far_nodes", "claire_set_tuning",
+    "claire_get_tuning",
 ]
 
 
@@ -114,6 +115,8 @@ def load_library(path=LIB_PATH):
         "claire_profile_read": ([P, ctypes.POINTER(KernelStat), I], I),
         "claire_transport_noalloc": ([I, I, I, I, P, P, P, P, ctypes.c_char_p, S], I),
         "claire_autotune": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "claire_set_tuning": ([P, I, I, I], I),
+        "claire_get_tuning": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "claire_solve_batch": ([ctypes.POINTER(P), I, ctypes.POINTER(D), I,
                                 ctypes.POINTER(P), ctypes.POINTER(Stats), I], I),
         "claire_conv3d_forward": ([P, I, I, I, I, I, P, P, I, I, P, P, P], I),
@@ -406,6 +409,18 @@ class Context:
         a, b = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.claire_autotune(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def set_tuning(self, sl_window=1, sl_t1=8, march_t1=32):
+        """Fix the tile shapes by hand (the SL gather variant, its x1 depth, the FD8
+        march depth)."""
+        self._check(self.lib.claire_set_tuning(self.h, sl_window, sl_t1, march_t1))
+
+    def tuning(self):
+        """(sl_window, sl_t1, march_t1) currently in use."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.claire_get_tuning(self.h, ctypes.byref(a), ctypes.byref(b),
+                                               ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     # -- launch accounting
     def far_nodes(self):

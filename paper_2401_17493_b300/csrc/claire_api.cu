@@ -1122,7 +1122,9 @@ claire_status autotune(claire_ctx* c) {
   tl_prof = nullptr;                                // tuning launches are not counted
   float best = 1e30f;
   Tuning t = c->tune;
-  for (int t1 : {4, 8, 16}) {
+  for (int variant = 0; variant < 6; ++variant) {
+    const int t1 = 4 << (variant % 3);
+    c->tune.sl_window = variant / 3;
     c->tune.sl_t1 = t1;
     float ms = 0.f;
     claire_status s = mixed(c)
@@ -1131,9 +1133,10 @@ claire_status autotune(claire_ctx* c) {
         : time_it([&] { launch_sl(c->g, c->mhist, c->df, nullptr, 1.f, nullptr, 0.f, c->pp0,
                                   c->st); }, &ms);
     if (s != CLAIRE_OK) { tl_prof = saved; return s; }
-    if (ms < best) { best = ms; t.sl_t1 = t1; }
+    if (ms < best) { best = ms; t.sl_t1 = t1; t.sl_window = c->tune.sl_window; }
   }
   c->tune.sl_t1 = t.sl_t1;
+  c->tune.sl_window = t.sl_window;
   best = 1e30f;
   if (march_supported(c->nt)) {
     for (int m1 : {8, 16, 32, 64}) {
@@ -1938,6 +1941,32 @@ claire_status claire_autotune(claire_ctx* c, int* sl_t1, int* march_t1) {
   if (!c->have_eval) TRY(evaluate(c));
   TRY(autotune(c));
   drop_graphs(c);                                  // captured with the previous shapes
+  if (sl_t1) *sl_t1 = c->tune.sl_t1;
+  if (march_t1) *march_t1 = c->tune.march_t1;
+  return CLAIRE_OK;
+}
+
+claire_status claire_set_tuning(claire_ctx* c, int sl_window, int sl_t1, int march_t1) {
+  if (!c) return CLAIRE_EINVAL;
+  ENTER(c);
+  if (sl_window != 0 && sl_window != 1)
+    return fail(c, CLAIRE_EINVAL, "sl_window must be 0 or 1");
+  if (sl_t1 != 4 && sl_t1 != 8 && sl_t1 != 16)
+    return fail(c, CLAIRE_EINVAL, "sl_t1 must be 4, 8 or 16");
+  if (march_t1 != 8 && march_t1 != 16 && march_t1 != 32 && march_t1 != 64)
+    return fail(c, CLAIRE_EINVAL, "march_t1 must be 8, 16, 32 or 64");
+  c->tune.sl_window = sl_window;
+  c->tune.sl_t1 = sl_t1;
+  c->tune.march_t1 = march_t1;
+  c->tuned = true;                                 // options.autotune keeps these shapes
+  drop_graphs(c);                                  // captured with the previous shapes
+  return CLAIRE_OK;
+}
+
+claire_status claire_get_tuning(const claire_ctx* c, int* sl_window, int* sl_t1,
+                                int* march_t1) {
+  if (!c) return CLAIRE_EINVAL;
+  if (sl_window) *sl_window = c->tune.sl_window;
   if (sl_t1) *sl_t1 = c->tune.sl_t1;
   if (march_t1) *march_t1 = c->tune.march_t1;
   return CLAIRE_OK;

@@ -42,14 +42,18 @@ struct Profiler {
 // The profiler of the context whose API call is running on this thread.
 extern thread_local Profiler* tl_prof;
 
-// Tile shapes picked by the autotuner for one grid: x1 depth of the SL brick
-// (4, 8 or 16 nodes) and planes per CTA of the FD8 march (8, 16, 32 or 64).
+// Tile shapes picked by the autotuner for one grid: the SL gather variant
+// (0: 64 shared loads per node, the default; 1: register window along x1 with
+// a deferred queue), the x1 depth of the SL brick (4, 8 or 16 nodes) and
+// planes per CTA of the FD8 march (8, 16, 32 or 64).
 struct Tuning {
+  int sl_window = 0;
   int sl_t1 = 8;
   int march_t1 = 32;
 };
 extern thread_local const Tuning* tl_tune;
 int tuned_sl_t1();
+bool tuned_sl_window();
 int tuned_march_t1();
 
 struct ProfileRange {

@@ -22,6 +22,7 @@
 #include "internal.h"
 #include "reduce.cuh"
 #include "sl_brick.cuh"
+#include "sl_window.cuh"
 #include "fd8_march.cuh"
 
 namespace claire {
@@ -150,6 +151,128 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl(Grid g, const float* __
       if (aux) r = fmaf(beta, ax, r);
     }
     out[idx] = r;
+  }
+}
+
+// ------------------------------------------------- SL step, x1 register window
+
+// The same SL step as k_sl with the register-window gather of sl_window.cuh:
+// the departure points and the epilogue operands of the tile are staged as
+// dense tiles beside the brick; each lane contracts the nodes that share its
+// reference floor from four x1 planes held in registers (one new plane of 16
+// shared loads per node instead of 64) and the rest are gathered from the
+// brick by the whole CTA afterwards.  Bitwise the same results as k_sl.
+template <int MODE>
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_slw(Grid g, const float* __restrict__ u,
+                                                    const float* __restrict__ d,
+                                                    const float* __restrict__ scale,
+                                                    float sigma,
+                                                    const float* __restrict__ aux, float beta,
+                                                    float ht, float* __restrict__ out,
+                                                    int t1) {
+  extern __shared__ __align__(16) float sm[];
+  float* td = sm + brick_floats(t1);                       // [3][t1][TB2][TB3]
+  float* tsc = td + 3 * tile_elems(t1);                    // scale tile (if any)
+  float* tax = tsc + (scale ? tile_elems(t1) : 0);         // aux tile (if any)
+  int* queue = reinterpret_cast<int*>(tax + (aux ? tile_elems(t1) : 0));
+  int* qcount = queue + tile_elems(t1);
+  const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const bool active = i2_0 + ty < g.n2 && i3_0 + lane < g.n3;
+  const int kmax = min(t1, g.n1 - i1_0);
+  if (ty == 0 && lane == 0) *qcount = 0;
+  stage_tile(d, g.N, 3, g, i1_0, i2_0, i3_0, t1, td);
+  if (MODE == 0 && scale) stage_tile(scale, g.N, 1, g, i1_0, i2_0, i3_0, t1, tsc);
+  if (MODE == 0 && aux) stage_tile(aux, g.N, 1, g, i1_0, i2_0, i3_0, t1, tax);
+  stage_brick(u, g, i1_0, i2_0, i3_0, sm, t1);
+  __syncthreads();
+  auto disp = [&](int k, int y, int l, float dd[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dd[a] = td[tile_at(t1, a, k, y, l)];
+  };
+  auto epi = [&](int k, int y, int l, float val) {
+    const int at = tile_at(t1, 0, k, y, l);
+    float r;
+    if (MODE == 1) {
+      const float x = sm[((k + HB_LO) * BB2 + y + HB_LO) * BB3 + l + HB3_LO];
+      r = 1.0f + 0.5f * ht * (val + x + ht * x * val);
+    } else {
+      r = val * (scale ? tsc[at] : sigma);
+      if (aux) r = fmaf(beta, tax[at], r);
+    }
+    out[lin(g, i1_0 + k, i2_0 + y, i3_0 + l)] = r;
+  };
+  int r1 = 0, r2 = 0, r3 = 0;
+  if (active) {
+    float dr[3];
+    disp(min(t1 / 2, kmax - 1), ty, lane, dr);
+    window_reference(dr[0], dr[1], dr[2], r1, r2, r3);
+  }
+  window_march(sm, kmax, ty, lane, active, r1, r2, r3, disp, epi, queue, qcount);
+  __syncthreads();
+  window_deferred(sm, i1_0, i2_0, i3_0, *qcount, queue, disp, epi,
+                  [&](const NodeTaps& t, int i1, int i2, int i3) {
+                    return gather_global(u, g, t, i1, i2, i3);
+                  });
+}
+
+// RK2 departure points of both directions (Sec. 2.5.2), register-window form
+// of k_trace: v of the tile is staged once as a dense tile; each velocity
+// component is staged once as a brick and gathered for both directions.
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_tracew(Grid g, const float* __restrict__ v,
+                                                       float* __restrict__ df,
+                                                       float* __restrict__ db, float ht,
+                                                       int t1) {
+  extern __shared__ __align__(16) float sm[];
+  float* tv = sm + brick_floats(t1);                       // [3][t1][TB2][TB3]
+  int* queue = reinterpret_cast<int*>(tv + 3 * tile_elems(t1));
+  int* qcount = queue + tile_elems(t1);                    // two counters, by pass parity
+  const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+  const int64_t N = g.N;
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const bool active = i2_0 + ty < g.n2 && i3_0 + lane < g.n3;
+  const int kmax = min(t1, g.n1 - i1_0);
+  if (ty == 0 && lane == 0) qcount[0] = qcount[1] = 0;
+  stage_tile(v, N, 3, g, i1_0, i2_0, i3_0, t1, tv);
+  const float ih[3] = {g.inv_h1, g.inv_h2, g.inv_h3};
+  int pass = 0;
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    if (c > 0) __syncthreads();                  // previous brick consumed
+    stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm, t1);
+    __syncthreads();
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      float* out = dir == 0 ? df : db;
+      if (out == nullptr) continue;
+      const float sg = dir == 0 ? -ht : ht;      // transport along +v / -v
+      int* qc = qcount + (pass & 1);
+      auto disp = [&](int k, int y, int l, float dd[3]) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dd[a] = sg * (tv[tile_at(t1, a, k, y, l)] * ih[a]);
+      };
+      const float ihc = c == 0 ? g.inv_h1 : (c == 1 ? g.inv_h2 : g.inv_h3);
+      auto epi = [&](int k, int y, int l, float w) {
+        const float uc = tv[tile_at(t1, c, k, y, l)] * ihc;
+        out[c * N + lin(g, i1_0 + k, i2_0 + y, i3_0 + l)] = 0.5f * sg * (uc + w * ihc);
+      };
+      int r1 = 0, r2 = 0, r3 = 0;
+      if (active) {
+        float dr[3];
+        disp(min(t1 / 2, kmax - 1), ty, lane, dr);
+        window_reference(dr[0], dr[1], dr[2], r1, r2, r3);
+      }
+      window_march(sm, kmax, ty, lane, active, r1, r2, r3, disp, epi, queue, qc);
+      __syncthreads();
+      const int nq = *qc;
+      if (ty == 0 && lane == 0) qcount[(pass + 1) & 1] = 0;   // the next pass's counter
+      window_deferred(sm, i1_0, i2_0, i3_0, nq, queue, disp, epi,
+                      [&](const NodeTaps& t, int i1, int i2, int i3) {
+                        return gather_global(v + c * N, g, t, i1, i2, i3);
+                      });
+      __syncthreads();                           // queue consumed before the next pass
+      ++pass;
+    }
   }
 }
 
@@ -733,6 +856,7 @@ static int vec_blocks(int64_t n) {
 
 thread_local const Tuning* tl_tune = nullptr;
 int tuned_sl_t1() { return tl_tune ? tl_tune->sl_t1 : TB1; }
+bool tuned_sl_window() { return tl_tune ? tl_tune->sl_window != 0 : false; }
 int tuned_march_t1() { return tl_tune ? tl_tune->march_t1 : MT1; }
 
 static void brick_attributes() {
@@ -742,6 +866,10 @@ static void brick_attributes() {
     cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_sl<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_sl<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    const int mw = window_smem_bytes(16, 5, 0);
+    cudaFuncSetAttribute(k_tracew, cudaFuncAttributeMaxDynamicSharedMemorySize, mw);
+    cudaFuncSetAttribute(k_slw<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mw);
+    cudaFuncSetAttribute(k_slw<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mw);
   });
 }
 void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht,
@@ -749,24 +877,37 @@ void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht,
   brick_attributes();
   const int t1 = tuned_sl_t1();
   ProfileRange pr(K_TRACE, (double)g.N * (12 + 12 * ((df != nullptr) + (db != nullptr))), st);
-  k_trace<<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-      g, v, df, db, ht, t1);
+  if (tuned_sl_window())
+    k_tracew<<<brick_grid(g, t1), dim3(32, TB2), window_smem_bytes(t1, 3, 0), st>>>(
+        g, v, df, db, ht, t1);
+  else
+    k_trace<<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
+        g, v, df, db, ht, t1);
 }
 void launch_sl(const Grid& g, const float* u, const float* d, const float* scale, float sigma,
                const float* aux, float beta, float* out, cudaStream_t st) {
   ProfileRange pr(K_SL, (double)g.N * (20 + 4 * (scale != nullptr) + 4 * (aux != nullptr)), st);
   brick_attributes();
   const int t1 = tuned_sl_t1();
-  k_sl<0><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-      g, u, d, scale, sigma, aux, beta, 0.f, out, t1);
+  if (tuned_sl_window())
+    k_slw<0><<<brick_grid(g, t1), dim3(32, TB2),
+               window_smem_bytes(t1, 3 + (scale != nullptr) + (aux != nullptr), 0), st>>>(
+        g, u, d, scale, sigma, aux, beta, 0.f, out, t1);
+  else
+    k_sl<0><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
+        g, u, d, scale, sigma, aux, beta, 0.f, out, t1);
 }
 void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float ht, float* c,
                            cudaStream_t st) {
   ProfileRange pr(K_ADJFAC, (double)g.N * 20, st);
   brick_attributes();
   const int t1 = tuned_sl_t1();
-  k_sl<1><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-      g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1);
+  if (tuned_sl_window())
+    k_slw<1><<<brick_grid(g, t1), dim3(32, TB2), window_smem_bytes(t1, 3, 0), st>>>(
+        g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1);
+  else
+    k_sl<1><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
+        g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1);
 }
 void launch_count_far(const Grid& g, const float* d, unsigned long long* out,
                       cudaStream_t st) {

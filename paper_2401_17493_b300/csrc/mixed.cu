@@ -22,6 +22,7 @@
 #include "internal.h"
 #include "reduce.cuh"
 #include "sl_brick.cuh"
+#include "sl_window.cuh"
 #include "fd8_march.cuh"
 
 namespace claire {
@@ -148,6 +149,57 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl_h(Grid g, const __half*
   }
 }
 
+// k_sl_h with the register-window gather (sl_window.cuh): the FP16 brick is
+// converted to FP32 while it is staged, then the gather is the FP32 window
+// march; the FP16 aux field is staged as a dense 16-bit tile.
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_slw_h(Grid g, const __half* __restrict__ u,
+                                                      const float* __restrict__ d,
+                                                      const float* __restrict__ scale,
+                                                      float sigma,
+                                                      const __half* __restrict__ aux,
+                                                      float beta, __half* __restrict__ out,
+                                                      int t1) {
+  extern __shared__ __align__(16) float smf[];
+  float* td = smf + brick_floats(t1);                      // [3][t1][TB2][TB3]
+  float* tsc = td + 3 * tile_elems(t1);                    // scale tile (if any)
+  __half* tax = reinterpret_cast<__half*>(tsc + (scale ? tile_elems(t1) : 0));
+  int* queue = reinterpret_cast<int*>(tax + (aux ? tile_elems(t1) : 0));
+  int* qcount = queue + tile_elems(t1);
+  const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const bool active = i2_0 + ty < g.n2 && i3_0 + lane < g.n3;
+  const int kmax = min(t1, g.n1 - i1_0);
+  if (ty == 0 && lane == 0) *qcount = 0;
+  stage_tile(d, g.N, 3, g, i1_0, i2_0, i3_0, t1, td);
+  if (scale) stage_tile(scale, g.N, 1, g, i1_0, i2_0, i3_0, t1, tsc);
+  if (aux) stage_tile(aux, g.N, 1, g, i1_0, i2_0, i3_0, t1, tax);
+  stage_brick_h32(u, g, i1_0, i2_0, i3_0, smf, t1);
+  cp_async_wait_all();              // the tiles' copies (the brick's scalar path issues none)
+  __syncthreads();
+  auto disp = [&](int k, int y, int l, float dd[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dd[a] = td[tile_at(t1, a, k, y, l)];
+  };
+  auto epi = [&](int k, int y, int l, float val) {
+    const int at = tile_at(t1, 0, k, y, l);
+    float r = val * (scale ? tsc[at] : sigma);
+    if (aux) r = fmaf(beta, __half2float(tax[at]), r);
+    out[lin(g, i1_0 + k, i2_0 + y, i3_0 + l)] = __float2half_rn(r);
+  };
+  int r1 = 0, r2 = 0, r3 = 0;
+  if (active) {
+    float dr[3];
+    disp(min(t1 / 2, kmax - 1), ty, lane, dr);
+    window_reference(dr[0], dr[1], dr[2], r1, r2, r3);
+  }
+  window_march(smf, kmax, ty, lane, active, r1, r2, r3, disp, epi, queue, qcount);
+  __syncthreads();
+  window_deferred(smf, i1_0, i2_0, i3_0, *qcount, queue, disp, epi,
+                  [&](const NodeTaps& t, int i1, int i2, int i3) {
+                    return gather_global_h(u, g, t, i1, i2, i3);
+                  });
+}
+
 // ------------------------------------------------------------------ small kernels
 
 // y = half(a x + b z) (z optional, FP16) -- conversions and the final
@@ -184,11 +236,18 @@ void launch_sl_h(const Grid& g, const __half* u, const float* d, const float* sc
   once_per_device(once, [] {
     cudaFuncSetAttribute(k_sl_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          brick_floats(16) * (int)sizeof(float));
+    cudaFuncSetAttribute(k_slw_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         window_smem_bytes(16, 4, 1));
   });
   const int t1 = tuned_sl_t1();
   ProfileRange pr(K_SL, (double)g.N * (16 + 4 * (scale != nullptr) + 2 * (aux != nullptr)), st);
-  k_sl_h<<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-      g, u, d, scale, sigma, aux, beta, out, t1);
+  if (tuned_sl_window())
+    k_slw_h<<<brick_grid(g, t1), dim3(32, TB2),
+              window_smem_bytes(t1, 3 + (scale != nullptr), aux != nullptr), st>>>(
+        g, u, d, scale, sigma, aux, beta, out, t1);
+  else
+    k_sl_h<<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
+        g, u, d, scale, sigma, aux, beta, out, t1);
 }
 
 template <int MODE>

@@ -58,6 +58,8 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.claire_create(896, 896, 896, 4, 1e-2, 1.0, ctypes.byref(h)) == claire.EINVAL
     assert h.value is None
     assert lib.claire_destroy(None) == claire.OK
+    assert lib.claire_set_tuning(None, 0, 8, 32) == claire.EINVAL
+    assert lib.claire_get_tuning(None, None, None, None) == claire.EINVAL
     assert lib.claire_last_error(None) == b"null context"
     # a wait budget outside 1 .. 2^20 polls is rejected before any launch
     assert lib.claire_wait_selftest(0, 0, None) == claire.EINVAL
