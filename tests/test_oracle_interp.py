@@ -3,6 +3,7 @@
 import numpy as np
 import pytest
 
+from oracle import interp as OI
 from oracle.interp import interp, interp_many, lagrange_weights
 
 
@@ -77,3 +78,18 @@ def test_many_fields_match_single_field_calls():
     many = interp_many(fs, q)
     for f, m in zip(fs, many):
         assert np.array_equal(interp(f, q), m)
+
+
+def test_threaded_chunks_give_bitwise_the_serial_values():
+    rng = np.random.default_rng(5)
+    shape = (40, 36, 48)
+    u = rng.standard_normal(shape)
+    q = np.stack(np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij"))
+    q = q + rng.uniform(-5.0, 5.0, size=(3,) + shape)
+    serial = OI.interp_many([u, -u], q)
+    try:
+        OI.set_threads(4)
+        threaded = OI.interp_many([u, -u], q)
+    finally:
+        OI.set_threads(1)
+    assert all(np.array_equal(a, b) for a, b in zip(serial, threaded))
