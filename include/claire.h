@@ -227,9 +227,8 @@ claire_status claire_det_deformation_gradient(claire_ctx* ctx, const float* v,
  * or fragmenting that pool, and some cannot accept the device-wide
  * synchronisation that cudaMalloc / cudaFree may imply.
  *
- * claire_transport_noalloc computes the same m(1) as claire_transport (RK2
- * departure points along +v, nt homogeneous SL steps, Sec. 2.5.2) with the same
- * kernels, without a context and without allocating: no cudaMalloc, no
+ * claire_transport_noalloc computes the same m(1) as claire_transport with the
+ * same kernels, without a context and without allocating: no cudaMalloc, no
  * cudaFree, no allocating library routine.  Its scratch (departure
  * displacements and one intermediate field, 16 bytes per voxel) is a
  * file-scope device array sized for CLAIRE_NOALLOC_MAX_VOXELS voxels
@@ -240,17 +239,23 @@ claire_status claire_det_deformation_gradient(claire_ctx* ctx, const float* v,
  *  m0      device [nx][ny][nz] float32 template (read only)
  *  m1_out  device [nx][ny][nz] float32 output; must not overlap m0 or v
  *  stream  cudaStream_t (NULL = legacy default stream); the call returns after
- *          synchronising that stream
+ *          synchronising that stream, so a stream that is capturing is refused
+ *          with CLAIRE_EINVAL before anything is launched
  *  err     optional buffer (may be NULL) that receives a message on failure
- * Sizes must be even and >= 16, 1 <= nt <= 256.
+ * Sizes must be even and >= 16, 1 <= nt <= 256.  v, m0 and m1_out must be
+ * device memory of the current device (checked; CLAIRE_EINVAL otherwise).
  *
  * The first call on a device looks up the device address of the scratch array
  * (cudaGetSymbolAddress) with that device current and caches it; make that
- * first call before any stream capture.  All calls in the process share the
- * one array per device and it keeps the last call's contents (every call
- * rewrites all of the scratch it reads, so nothing needs clearing); calls that
- * overlap on the same GPU (other streams or threads) race on it, so callers
- * must serialise them. */
+ * first call before any stream capture.  With lazy module loading (the CUDA
+ * default) that first lookup is also when the driver loads this part of the
+ * library onto the device and commits the 16 MiB array, so a caller whose
+ * device memory is reserved afterwards should make one call first; the calls
+ * after it commit nothing.  A failed lookup is not cached: the next call
+ * retries it.  All calls in the process share the one array per device and
+ * it keeps the last call's contents (every call rewrites all of the scratch
+ * it reads, so nothing needs clearing); calls that overlap on the same GPU
+ * (other streams or threads) race on it, so callers must serialise them. */
 #define CLAIRE_NOALLOC_MAX_VOXELS (1LL << 20)
 claire_status claire_transport_noalloc(int nx, int ny, int nz, int nt, const float* v,
                                        const float* m0, float* m1_out, void* stream,

@@ -193,12 +193,16 @@ def transport_noalloc(v, m0, out, nt=4, stream=None):
     import torch
     L = load_library()
     shape = tuple(m0.shape)
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    buf = ctypes.create_string_buffer(512)
-    st = L.claire_transport_noalloc(*shape, int(nt), _ptr(v, (3,) + shape, "v"),
-                                    _ptr(m0, shape, "m0"), _ptr(out, shape, "out"),
-                                    ctypes.c_void_p(stream.cuda_stream), buf, 512)
+    for t, name in ((v, "v"), (m0, "m0"), (out, "out")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == m0.device):
+            raise ValueError(f"{name} must be a CUDA tensor on the device of m0")
+    with torch.cuda.device(m0.device):
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        buf = ctypes.create_string_buffer(512)
+        st = L.claire_transport_noalloc(*shape, int(nt), _ptr(v, (3,) + shape, "v"),
+                                        _ptr(m0, shape, "m0"), _ptr(out, shape, "out"),
+                                        ctypes.c_void_p(stream.cuda_stream), buf, 512)
     if st != OK:
         raise ClaireError(st, buf.value.decode())
     return out

@@ -29,12 +29,21 @@ constexpr long long kFloatsPerVoxel = 4;
 static __device__ __align__(256) float g_noalloc_scratch[kFloatsPerVoxel * CLAIRE_NOALLOC_MAX_VOXELS];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-float* g_scratch_ptr[kMaxDevices] = {};
-cudaError_t g_setup_err[kMaxDevices] = {};
+std::mutex g_setup_mutex;
+float* g_scratch_ptr[kMaxDevices] = {};   // set once a lookup on that device succeeded
 
 void set_error(char* err, size_t len, const char* fmt, long long a = 0, long long b = 0) {
   if (err && len > 0) snprintf(err, len, fmt, a, b);
+}
+
+// True when p is device memory of device dev (not host, managed or another GPU's memory).
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();                   // clear the error state of the failed query
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
@@ -71,26 +80,50 @@ extern "C" claire_status claire_transport_noalloc(int nx, int ny, int nz, int nt
     set_error(err, err_len, "claire_transport_noalloc: m1_out overlaps m0 or v");
     return CLAIRE_EINVAL;
   }
-  // Set-up, once per device with that device current: the host-side name of
-  // the array is not a device address, so look the address up and cache it.
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     set_error(err, err_len, "claire_transport_noalloc: cudaGetDevice failed or device >= 64");
     return CLAIRE_ECUDA;
   }
-  std::call_once(g_once[dev], [dev]() {
-    void* p = nullptr;
-    g_setup_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    g_scratch_ptr[dev] = (float*)p;
-  });
-  if (g_setup_err[dev] != cudaSuccess || g_scratch_ptr[dev] == nullptr) {
-    if (err && err_len > 0)
-      snprintf(err, err_len, "claire_transport_noalloc: cudaGetSymbolAddress failed: %s",
-               cudaGetErrorString(g_setup_err[dev]));
-    return CLAIRE_ECUDA;
+  // The kernels run on the current device: every array must live there.
+  if (!on_device(v, dev) || !on_device(m0, dev) || !on_device(m1_out, dev)) {
+    set_error(err, err_len,
+              "claire_transport_noalloc: v, m0 and m1_out must be device memory of the current "
+              "device (%lld)", dev);
+    return CLAIRE_EINVAL;
   }
-  float* d = g_scratch_ptr[dev];          // [3][N] displacements, fully rewritten below
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    if (e != cudaSuccess) cudaGetLastError();
+    set_error(err, err_len,
+              "claire_transport_noalloc: the call synchronises its stream before returning, "
+              "which a capturing stream does not allow");
+    return CLAIRE_EINVAL;
+  }
+  // Set-up per device, with that device current: the host-side name of the
+  // array is not a device address, so look the address up and cache it.  Only
+  // a successful lookup is cached; a failed one is retried on the next call.
+  float* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (g_scratch_ptr[dev] == nullptr) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        if (err && err_len > 0)
+          snprintf(err, err_len, "claire_transport_noalloc: cudaGetSymbolAddress failed: %s",
+                   cudaGetErrorString(e));
+        return CLAIRE_ECUDA;
+      }
+      g_scratch_ptr[dev] = (float*)p;
+    }
+    scratch = g_scratch_ptr[dev];
+  }
+  float* d = scratch;                     // [3][N] displacements, fully rewritten below
   float* tmp = d + 3 * N;                 // [N] intermediate state, fully rewritten below
 
   Grid g{};
@@ -100,7 +133,6 @@ extern "C" claire_status claire_transport_noalloc(int nx, int ny, int nz, int nt
   g.h1 = (float)(tp / nx); g.h2 = (float)(tp / ny); g.h3 = (float)(tp / nz);
   g.inv_h1 = (float)(nx / tp); g.inv_h2 = (float)(ny / tp); g.inv_h3 = (float)(nz / tp);
   const float ht = 1.0f / (float)nt;
-  cudaStream_t st = (cudaStream_t)stream;
 
   // Same kernels as claire_transport: RK2 departure points along +v, then nt
   // homogeneous SL steps.  Step j writes m1_out when nt-1-j is even, else the

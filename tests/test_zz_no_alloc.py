@@ -77,3 +77,28 @@ def test_noalloc_transport_rejects_grids_beyond_its_limit(lib):
     # aliasing the output with the input is refused as well
     st, msg = _call(C, (16, 16, 16), 4, v, m0, m0)
     assert st == C.EINVAL and "overlaps" in msg
+
+
+def test_noalloc_transport_refuses_memory_that_is_not_on_the_current_device(lib):
+    C = lib
+    shape = (16, 16, 16)
+    v = torch.zeros((3,) + shape, device="cuda")
+    m0 = torch.zeros(shape, device="cuda")
+    out = torch.zeros(shape, device="cuda")
+    pinned = torch.zeros(shape, pin_memory=True)
+    pageable = np.zeros(shape, dtype=np.float32)
+    buf = ctypes.create_string_buffer(512)
+    L = C.load_library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # nothing is launched: the pointers are checked first
+    st = L.claire_transport_noalloc(*shape, 4, ctypes.c_void_p(v.data_ptr()),
+                                    ctypes.c_void_p(pinned.data_ptr()),
+                                    ctypes.c_void_p(out.data_ptr()), stream, buf, 512)
+    assert st == C.EINVAL and "device memory of the current device" in buf.value.decode()
+    st = L.claire_transport_noalloc(*shape, 4, ctypes.c_void_p(v.data_ptr()),
+                                    ctypes.c_void_p(m0.data_ptr()),
+                                    ctypes.c_void_p(pageable.ctypes.data), stream, buf, 512)
+    assert st == C.EINVAL and "device memory of the current device" in buf.value.decode()
+    # the entry point still works afterwards
+    st, msg = _call(C, shape, 4, v, m0, out)
+    assert st == C.OK, msg
