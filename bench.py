@@ -13,7 +13,11 @@ Printed (rank 0, one JSON line): solve seconds per registration (value), plus
 Hessian matvecs/s at 256^3, the interpolation + FD8 share of HBM peak, the
 roofline of the dominant kernel (event-timed inside the timed solves), the
 end-to-end number through the host-buffer C entry point, clocks sampled
-during the timed region, and the FP64 CPU oracle as a bounded sample.
+during the timed region, per-level counts of the continuation and the solve
+under the other reading of its stopping denominator, the plain FP32 solver
+against the mixed + warm-started + batched form on held-out 128^3 pairs (with
+a U-Net trained in this run), the 768^3 registration, and the FP64 CPU oracle
+timed at 256^3 on the host cores.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 With N > 1 (torchrun) every rank registers its own pair: replicas only, no
@@ -38,13 +42,19 @@ MAX_PCG = 200
 SEED = 2
 PRECOND = 1                # two-level zero-velocity preconditioner (Sec. 2.5.6, 2.6)
 MAX_INNER = 10             # nested CG cap per preconditioner application
-CPU_SAMPLE_N = 32          # oracle sample: the workload restricted to 32^3
 INTERP_FD = ("trace", "sl_step", "adjoint_factor", "grad8", "div8", "sdot_hist", "accum_hist")
 # DRAM traffic per voxel and launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) for the kernels below, from the capture summarised in
-# profiles/k_sl_256cube.md (matvec SL steps, 24 algorithmic B/voxel); drop an
-# entry when its kernel changes.
-NCU_TRAFFIC_PER_VOXEL = {"sl_step": 23.25}
+# dram__bytes_write.sum over the matvec's SL steps at 256^3, 24 algorithmic
+# B/voxel), with the SHA-256 of the kernel's source (its function in kernels.cu
+# plus sl_brick.cuh and common.cuh) at the time of the capture: when the source
+# differs, the figure is stale and roofline.traffic is reported as null.
+NCU_TRAFFIC_PER_VOXEL = {
+    "sl_step": (23.25, "5cfa7294c2162eb5b56eedcdcdd1681bef9ff3fc472cb3a7a02306694b6874d8")}
+# 64-tap gathers of a field per 256^3 registration of the headline solve (trace
+# components x directions + SL steps + adjoint factors), counted by the
+# library's launch profile in this bench's own arm ("field_gathers_per_registration"):
+# the reference arm scales its per-gather time by it.
+GATHERS_PER_REGISTRATION = 0
 
 
 def parse():
@@ -58,6 +68,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-pair batched workload")
     ap.add_argument("--batch-pairs", type=int, default=32)
+    ap.add_argument("--no-combined", action="store_true",
+                    help="skip the plain vs mixed + warm start + batched comparison")
+    ap.add_argument("--combined-train", type=int, default=512,
+                    help="solver-generated 128^3 training pairs of the bench's U-Net")
+    ap.add_argument("--combined-epochs", type=int, default=30)
+    ap.add_argument("--combined-eval", type=int, default=64, help="held-out pairs")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 768^3 registration")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay the PCG parts of the 256^3 solves as CUDA graphs (default); 0 "
                          "launches every kernel (profilers list the kernels inside graphs that "
@@ -153,9 +170,9 @@ class ClockSampler:
 
 
 def workload(n):
+    """The headline pair and the velocity that generated m1 (float32)."""
     from paper_2401_17493_b300 import synth
-    m0, m1, _ = synth.ellipsoid_pair((n, n, n), seed=SEED)
-    return m0, m1
+    return synth.ellipsoid_pair((n, n, n), seed=SEED)
 
 
 BATCH_GRIDS = [(64, 64, 64), (96, 112, 80), (128, 128, 128), (160, 192, 144), (192, 192, 192)]
@@ -228,57 +245,246 @@ def run_batch(args, pairs):
                         "two-level preconditioner"}
 
 
-def cpu_oracle_sample(m0, m1, n_full):
-    """FP64 oracle continuation solve of the workload restricted to 32^3, scaled by
-    the voxel ratio to the full grid (the 256^3 solve takes more iterations, so the
-    scaled figure underestimates the CPU time).  Returns (scaled s, measured s,
-    stats, threads used = process CPU time / wall time, rounded, at least 1)."""
+def sl_source_sha():
+    """SHA-256 of the SL step's source: its kernel function in kernels.cu (from
+    its comment block to the closing brace), sl_brick.cuh and common.cuh."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2401_17493_b300", "csrc")
+    try:
+        k = open(os.path.join(csrc, "kernels.cu")).read()
+        m = re.search(r"// MODE 0: out = .*?\n}\n", k, flags=re.S)
+        if m is None:
+            return None
+        h = hashlib.sha256(m.group(0).encode())
+        for f in ("sl_brick.cuh", "common.cuh"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        return h.hexdigest()
+    except OSError:
+        return None
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def set_oracle_threads(t):
+    from oracle import fd8, interp, spectral
+    interp.set_threads(t)
+    fd8.set_threads(t)
+    spectral.WORKERS = t
+
+
+def pick_oracle_threads():
+    """All usable host CPUs, or half of them when that gathers a 96^3 field
+    faster (the gathers are memory-bound; on some hosts fewer threads win)."""
     import numpy as np
-    from oracle import reduced, solver, spectral
-    ns = CPU_SAMPLE_N
-    a = spectral.restrict(m0.astype(np.float64), (ns,) * 3)
-    b = spectral.restrict(m1.astype(np.float64), (ns,) * 3)
-    t0, c0 = time.perf_counter(), time.process_time()
-    prob = reduced.Problem(a, b, nt=NT, beta_v=BETAS[0])
-    _, st, _ = solver.continuation(prob, BETAS, solver.Options(
-        eps_opt=EPS_OPT, max_pcg=MAX_PCG, precond="two_level" if PRECOND else "spectral",
-        max_inner=MAX_INNER))
-    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
-    scale = (n_full / ns) ** 3
-    return dt * scale, dt, st, max(1, int(round(cpu / dt)))
+    from oracle import interp
+    full = host_threads()
+    rng = np.random.default_rng(0)
+    n = 96
+    u = rng.standard_normal((n,) * 3)
+    q = np.stack(np.meshgrid(*[np.arange(n, dtype=float)] * 3, indexing="ij"))
+    q = q + rng.uniform(-2.0, 2.0, size=(3, n, n, n))
+    best = None
+    for t in sorted({full, max(1, full // 2)}, reverse=True):
+        interp.set_threads(t)
+        t0 = time.perf_counter()
+        interp.interp(u, q)
+        dt = time.perf_counter() - t0
+        if best is None or dt < best[1]:
+            best = (t, dt)
+    interp.set_threads(1)
+    return best[0]
+
+
+def cpu_oracle_units(m0, m1, v, vt, beta):
+    """The FP64 oracle at the full grid on the host cores: one transport m(1)
+    (trace + nt SL steps), one objective + gradient evaluation (state, adjoint,
+    gradient), one Gauss-Newton Hessian matvec.  Returns seconds of each, the
+    threads used and the threads kept busy (process CPU time / wall time)."""
+    import numpy as np
+    from oracle import reduced, transport
+    threads = pick_oracle_threads()
+    set_oracle_threads(threads)
+    a, b = m0.astype(np.float64), m1.astype(np.float64)
+    v, vt = v.astype(np.float64), vt.astype(np.float64)
+    c0, t0 = time.process_time(), time.perf_counter()
+    transport.state_solve(a, v, NT)
+    t1 = time.perf_counter()
+    prob = reduced.Problem(a, b, nt=NT, beta_v=beta)
+    ev = reduced.evaluate(prob, v)
+    t2 = time.perf_counter()
+    reduced.hessian_matvec(prob, ev, vt)
+    t3 = time.perf_counter()
+    busy = (time.process_time() - c0) / (t3 - t0)
+    set_oracle_threads(1)
+    return {"transport_s": t1 - t0, "gradient_s": t2 - t1, "matvec_s": t3 - t2,
+            "threads": threads, "busy": busy}
+
+
+def oracle_registration_estimate(u, st, levels):
+    """Seconds of the oracle's own registration with the GPU solve's counts: one
+    evaluation at v = 0 and one per level start, per Newton step the gradient
+    completion (an evaluation minus its state solve) and the Armijo trial state
+    solves, plus the matvecs.  The nested coarse-grid CG of the two-level
+    preconditioner is not counted."""
+    n_gn = st["newton_iters"]
+    trials = n_gn + st.get("linesearch_halvings", 0)
+    return ((1 + levels) * u["gradient_s"] + n_gn * (u["gradient_s"] - u["transport_s"]) +
+            trials * u["transport_s"] + st["matvecs"] * u["matvec_s"])
 
 
 def run_reference(args, world, rank):
+    """The oracle arm: each step is one FP64 SL step of the headline workload at
+    its full grid (the 64-tap gather of m0 at the RK2 departure points of the
+    velocity that generated m1), on the host cores.  value / ms_per_step are the
+    time that step took; the registration estimate is a separate key."""
     if rank != 0:
         return
     import numpy as np
+    from oracle import interp, transport
     n = args.size
-    m0, m1 = workload(n)
+    m0, m1, v = workload(n)
+    threads = pick_oracle_threads()
+    set_oracle_threads(threads)
+    m0 = m0.astype(np.float64)
+    y = transport.departure_points(v.astype(np.float64), NT, +1)     # untimed, once
     for _ in range(args.warmup):
-        cpu_oracle_sample(m0, m1, n)
-    vals, raw, used = [], [], []
+        interp.interp(m0, y)
+    times, busy = [], []
     for _ in range(args.steps):
-        v, dt, st, th = cpu_oracle_sample(m0, m1, n)
-        vals.append(v)
-        raw.append(dt)
-        used.append(th)
-    value = float(np.mean(vals))
-    cores = max(used)
-    sample = (f"oracle FP64 continuation solve of the {CPU_SAMPLE_N}^3 spectral restriction of "
-              f"the {n}^3 pair ({np.mean(raw):.2f} s per solve), scaled x{(n // CPU_SAMPLE_N) ** 3}"
-              f" by voxel count; {cores} thread(s) busy of {os.cpu_count()} logical CPUs")
-    print(json.dumps({
+        c0, t0 = time.process_time(), time.perf_counter()
+        interp.interp(m0, y)
+        dt = time.perf_counter() - t0
+        times.append(dt)
+        busy.append((time.process_time() - c0) / dt)
+    value = float(np.mean(times))
+    cores = int(round(max(busy)))
+    sample = (f"one FP64 oracle SL step (64-tap gather of the {n}^3 template at the RK2 "
+              f"departure points of the workload's velocity) per step, {threads} threads of "
+              f"{host_threads()} host CPUs, {cores} kept busy")
+    line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{n}^3 ellipsoid phantom pair, continuation 1e-1..1e-4, nt 4, "
-                               "two-level preconditioner",
-                   "sample": f"{CPU_SAMPLE_N}^3"},
+        "config": {"workload": f"{n}^3 ellipsoid phantom pair (seed {SEED}), nt 4",
+                   "sample": "one SL step per step (not a registration)"},
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }), flush=True)
+    }
+    if GATHERS_PER_REGISTRATION > 0:
+        line["registration_estimate"] = {
+            "value": value * GATHERS_PER_REGISTRATION, "unit": "s",
+            "basis": f"per-gather time x {GATHERS_PER_REGISTRATION} field gathers of one GPU "
+                     "registration of this workload (an extrapolation, not a measurement)"}
+    print(json.dumps(line), flush=True)
+
+
+def continuation_levels(ctx, betas, reps):
+    """Per-level counts of the continuation, and the solve under the other
+    reading of its stopping rule.
+
+    reading C-10 (the headline): every level stops at eps_opt ||g(v = 0)||_inf;
+    own-start reading: each level stops at eps_opt ||g(v_start)||_inf, v_start
+    the level's warm start (its gradient evaluated with the level's beta_v).
+    Both run level by level (claire_solve per level); the other reading is also
+    timed (reps solves after one warm-up, CUDA events, the per-level gradient
+    evaluations included) and its final gradient is also given relative to
+    ||g(v = 0)||_inf."""
+    import torch
+    shape = ctx.shape
+    stream = torch.cuda.current_stream()
+    v = torch.zeros((3,) + shape, device="cuda")
+    ctx.set_beta(betas[0])
+    _, g = ctx.objective_gradient(v)
+    g0 = float(g.abs().max())
+    levels = []
+    for b in betas:
+        ctx.set_beta(b)
+        ctx.set_options(gnorm0=g0)
+        _, st = ctx.solve(v)
+        levels.append({"beta_v": b, "newton_iters": st.newton_iters, "matvecs": st.matvecs,
+                       "grad_rel": st.grad_rel, "mismatch_rel": st.mismatch_rel})
+
+    def own_start():
+        v.zero_()
+        out = []
+        for b in betas:
+            ctx.set_beta(b)
+            ctx.set_options(gnorm0=0.0)
+            _, gs = ctx.objective_gradient(v)
+            ctx.set_options(gnorm0=float(gs.abs().max()))
+            _, st = ctx.solve(v)
+            out.append(st)
+        return out
+
+    own_start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        sts = own_start()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _, gf = ctx.objective_gradient(v)
+    ctx.set_options(gnorm0=0.0)
+    ctx.set_beta(betas[0])
+    return {
+        "denominator_g0": {"levels": levels},
+        "denominator_own_start": {
+            "seconds": e0.elapsed_time(e1) / 1e3 / reps, "reps": reps,
+            "levels": [{"beta_v": b, "newton_iters": st.newton_iters, "matvecs": st.matvecs,
+                        "grad_rel_own": st.grad_rel, "mismatch_rel": st.mismatch_rel}
+                       for b, st in zip(betas, sts)],
+            "newton_iters": sum(st.newton_iters for st in sts),
+            "matvecs": sum(st.matvecs for st in sts),
+            "mismatch_rel": sts[-1].mismatch_rel,
+            "grad_rel_vs_g0": float(gf.abs().max()) / g0},
+    }
+
+
+def run_combined(args):
+    """The plain FP32 solver (zero initial guess, pairs one after another)
+    against mixed precision + U-Net warm start + batched solves on held-out
+    128^3 pairs (unet.evaluate_combined), with a U-Net trained here on
+    solver-generated pairs: seeds 10000.. for training, 20000.. held out,
+    beta_v 1e-2, rel-grad 5e-2 with the same denominator for both arms."""
+    import torch
+    from paper_2401_17493_b300 import unet
+    n, beta = 128, 1e-2
+    t0 = time.perf_counter()
+    inputs, targets = [], []
+    seeds = list(range(10000, 10000 + args.combined_train))
+    for i in range(0, len(seeds), 64):
+        pairs = unet.make_pairs(seeds[i:i + 64], n)
+        vs = unet.solve_targets(pairs, n, beta)
+        for (m0, m1), v in zip(pairs, vs):
+            inputs.append(unet.resample(torch.stack([m0, m1]).contiguous(), (n,) * 3,
+                                        (64,) * 3, 2))
+            targets.append(unet.resample(v.contiguous(), (n,) * 3, (64,) * 3, 3))
+        del pairs, vs
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    model = unet.UNet3D(seed=0)
+    t0 = time.perf_counter()
+    hist = unet.train(model, inputs, targets, args.combined_epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del inputs, targets
+    held = unet.make_pairs(list(range(20000, 20000 + args.combined_eval)), n)
+    res = unet.evaluate_combined(model, held, n, beta, batch=min(64, args.combined_eval))
+    res.update({"grid": n, "beta_v": beta, "train_pairs": args.combined_train,
+                "epochs": args.combined_epochs, "train_s": t_train, "targets_s": t_data,
+                "final_loss": hist[-1] if hist else None,
+                "target_2x_met": bool(res["speedup"] >= 2.0)})
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_claire(args, world, rank, local):
@@ -293,7 +499,7 @@ def run_claire(args, world, rank, local):
     build.build()
     n = args.size
     shape = (n, n, n)
-    m0, m1 = workload(n)
+    m0, m1, v_gen = workload(n)
     pairs = None
     if not args.no_batch and rank == 0 and world == 1:
         pairs = batch_workload(args.batch_pairs)     # before any CUDA call of this process
@@ -414,6 +620,13 @@ def run_claire(args, world, rank, local):
     m_ms = sum(mprof[k]["ms"] for k in INTERP_FD if k in mprof)
     matvec_interp_gbs = m_bytes / (m_ms * 1e-3) / 1e9 if m_ms > 0 else None
 
+    # per-level counts (reading C-10) and the solve under the own-start reading
+    levels = continuation_levels(ctx, BETAS, max(1, min(args.steps, 5)))
+    levels["headline_levels_match"] = (
+        sum(lv["newton_iters"] for lv in levels["denominator_g0"]["levels"]) ==
+        stats[-1]["newton_iters"] and
+        sum(lv["matvecs"] for lv in levels["denominator_g0"]["levels"]) == stats[-1]["matvecs"])
+
     # end to end through the host-buffer entry point: H2D m0, m1, v; solve; D2H v
     m0h = torch.from_numpy(m0).pin_memory()
     m1h = torch.from_numpy(m1).pin_memory()
@@ -434,23 +647,54 @@ def run_claire(args, world, rank, local):
     # launches replayed inside captured graphs are counted, not timed: the rate is
     # the timed launches' algorithmic bytes over their event-timed duration
     achieved = d["timed_bytes"] / (d["ms"] * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC_PER_VOXEL.get(dom)
+    traffic = None
+    if dom in NCU_TRAFFIC_PER_VOXEL and NCU_TRAFFIC_PER_VOXEL[dom][1] == sl_source_sha():
+        traffic = NCU_TRAFFIC_PER_VOXEL[dom][0]
+    # 64-tap field gathers per registration: 3 per trace direction (a trace launch
+    # moves 12 + 12 x directions bytes per voxel), one per SL step / adjoint factor
+    tr = prof.get("trace", {"bytes": 0.0, "launches": 0})
+    gathers = ((tr["bytes"] / n ** 3 - 12 * tr["launches"]) / 4 +
+               prof.get("sl_step", {"launches": 0})["launches"] +
+               prof.get("adjoint_factor", {"launches": 0})["launches"]) / args.steps
     interp_bytes = sum(mine[k]["timed_bytes"] for k in INTERP_FD if k in mine)
     interp_ms = sum(mine[k]["ms"] for k in INTERP_FD if k in mine)
     interp_gbs = interp_bytes / (interp_ms * 1e-3) / 1e9
     total_kernel_ms = sum(p["ms"] for p in prof.values())
 
+    v_final = v_fp32.cpu().numpy()
+    vt_host = vt.cpu().numpy()
+    st0 = stats[-1]
+    workspace_gb = ctx.workspace_bytes / 1e9
+    ctx.close()
+    del m0d, m1d, v, vs_, vm, vt, out, v_fp32
+    torch.cuda.empty_cache()
+
     batch = run_batch(args, pairs) if pairs is not None else None
+    combined = None
+    if rank == 0 and world == 1 and not args.no_combined:
+        combined = run_combined(args)
+    scale = None
+    if rank == 0 and world == 1 and not args.no_scale and n == 256:
+        from paper_2401_17493_b300 import scale_run
+        scale = scale_run.run(768, precision=1, beta=1e-3, matvecs=10, precond=PRECOND, solves=2)
+        scale.pop("kernels", None)
+        scale["workload"] = ("768^3 ellipsoid phantom pair (seed 3), FP16 histories, nt 4, "
+                             "beta_v 1e-3, rel-grad 5e-2, two-level preconditioner; one "
+                             "untimed warm-up solve, one timed")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, raw, _, used = cpu_oracle_sample(m0, m1, n)
-        cpu = {"value": est, "unit": "s", "cores": used, "kind": "oracle",
-               "sample": f"oracle FP64 continuation solve of the {CPU_SAMPLE_N}^3 restriction "
-                         f"({raw:.2f} s), scaled x{(n // CPU_SAMPLE_N) ** 3} by voxel count; "
-                         f"{used} thread(s) busy of {os.cpu_count()} logical CPUs"}
+        units = cpu_oracle_units(m0, m1, v_final, vt_host, BETAS[-1])
+        est = oracle_registration_estimate(units, st0, len(BETAS))
+        cpu = {"value": est, "unit": "s", "cores": int(round(units["busy"])), "kind": "oracle",
+               "sample": (f"FP64 oracle at {n}^3 on {units['threads']} threads of "
+                          f"{host_threads()} host CPUs ({units['busy']:.1f} kept busy): one "
+                          f"transport {units['transport_s']:.1f} s, one objective+gradient "
+                          f"{units['gradient_s']:.1f} s, one GN matvec {units['matvec_s']:.1f} s "
+                          "(measured, at the converged velocity); value = those unit costs x "
+                          "the timed GPU solve's counts (evaluations, Armijo trials, matvecs)"),
+               "units": units}
 
-    st0 = stats[-1]
     line = {
         "metric": METRIC, "value": s_per_solve, "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -460,12 +704,16 @@ def run_claire(args, world, rank, local):
                                "1e-1..1e-4, rel-grad 5e-2 per level, nt 4, H1 seminorm, FP32, "
                                "two-level zero-velocity preconditioner" +
                                (", PCG parts replayed as CUDA graphs" if args.graphs else ""),
-                   "l2": "working set ~%.1f GB > 126 MB L2" % (ctx.workspace_bytes / 1e9),
+                   "l2": "working set ~%.1f GB > 126 MB L2" % workspace_gb,
                    "parallelism": "replicas" if world > 1 else "single"},
         "matvecs_per_s": matvecs_per_s,
         "spectral_preconditioner": spectral_pc,
         "mixed": mixed,
         "batch": batch,
+        "continuation": levels,
+        "combined": combined,
+        "scale_768": scale,
+        "field_gathers_per_registration": gathers,
         "interp_fd_hbm_frac": interp_gbs / peak,
         "interp_fd_gbs": interp_gbs,
         "matvec_interp_fd_hbm_frac": None if matvec_interp_gbs is None else matvec_interp_gbs / peak,
@@ -479,6 +727,8 @@ def run_claire(args, world, rank, local):
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None if traffic is None else traffic * n ** 3,
+                     "traffic_source": "ncu dram bytes of this kernel source" if traffic
+                     else "null: the kernel source changed since the ncu capture",
                      "peak_source": peak_src,
                      "share_of_timed_kernel_time": d["ms"] / total_kernel_ms},
         "kernels": {k: {"launches": p["launches"], "timed": p["timed"], "ms": round(p["ms"], 3),
@@ -493,7 +743,6 @@ def run_claire(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -71,3 +71,17 @@ def test_gradient_and_divergence_are_negative_adjoints():
     lhs = np.sum(grad8(u) * w)
     rhs = -np.sum(u * div8(w))
     assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_threaded_slabs_give_bitwise_the_serial_values():
+    from oracle import fd8 as F
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((72, 64, 80))
+    w = rng.standard_normal((3, 72, 64, 80))
+    serial_g, serial_d = F.grad8(u), F.div8(w)
+    try:
+        F.set_threads(5)
+        threaded_g, threaded_d = F.grad8(u), F.div8(w)
+    finally:
+        F.set_threads(1)
+    assert np.array_equal(serial_g, threaded_g) and np.array_equal(serial_d, threaded_d)
