@@ -54,7 +54,7 @@ NCU_TRAFFIC_PER_VOXEL = {
 # components x directions + SL steps + adjoint factors), counted by the
 # library's launch profile in this bench's own arm ("field_gathers_per_registration"):
 # the reference arm scales its per-gather time by it.
-GATHERS_PER_REGISTRATION = 0
+GATHERS_PER_REGISTRATION = 161
 
 
 def parse():
@@ -70,10 +70,10 @@ def parse():
     ap.add_argument("--batch-pairs", type=int, default=32)
     ap.add_argument("--no-combined", action="store_true",
                     help="skip the plain vs mixed + warm start + batched comparison")
-    ap.add_argument("--combined-train", type=int, default=512,
+    ap.add_argument("--combined-train", type=int, default=2000,
                     help="solver-generated 128^3 training pairs of the bench's U-Net")
-    ap.add_argument("--combined-epochs", type=int, default=30)
-    ap.add_argument("--combined-eval", type=int, default=64, help="held-out pairs")
+    ap.add_argument("--combined-epochs", type=int, default=40)
+    ap.add_argument("--combined-eval", type=int, default=200, help="held-out pairs")
     ap.add_argument("--no-scale", action="store_true", help="skip the 768^3 registration")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay the PCG parts of the 256^3 solves as CUDA graphs (default); 0 "
@@ -454,7 +454,9 @@ def run_combined(args):
     against mixed precision + U-Net warm start + batched solves on held-out
     128^3 pairs (unet.evaluate_combined), with a U-Net trained here on
     solver-generated pairs: seeds 10000.. for training, 20000.. held out,
-    beta_v 1e-2, rel-grad 5e-2 with the same denominator for both arms."""
+    beta_v 1e-2, rel-grad 5e-2 with the same denominator for both arms.  The
+    default recipe (2000 pairs, 40 epochs, 200 held out) is the learned warm
+    start's own; smaller ones train faster and gain less."""
     import torch
     from paper_2401_17493_b300 import unet
     n, beta = 128, 1e-2
@@ -479,6 +481,7 @@ def run_combined(args):
     del inputs, targets
     held = unet.make_pairs(list(range(20000, 20000 + args.combined_eval)), n)
     res = unet.evaluate_combined(model, held, n, beta, batch=min(64, args.combined_eval))
+    del held
     res.update({"grid": n, "beta_v": beta, "train_pairs": args.combined_train,
                 "epochs": args.combined_epochs, "train_s": t_train, "targets_s": t_data,
                 "final_loss": hist[-1] if hist else None,
@@ -681,6 +684,12 @@ def run_claire(args, world, rank, local):
         scale["workload"] = ("768^3 ellipsoid phantom pair (seed 3), FP16 histories, nt 4, "
                              "beta_v 1e-3, rel-grad 5e-2, two-level preconditioner; one "
                              "untimed warm-up solve, one timed")
+        f32 = scale_run.run(768, precision=0, beta=1e-3, matvecs=10, precond=PRECOND, solves=2)
+        scale["fp32_storage"] = {k: f32[k] for k in ("solve_s", "newton_iters", "matvecs",
+                                                     "grad_rel", "mismatch_rel", "matvecs_per_s",
+                                                     "workspace_gb", "device_used_gb")}
+        scale["mixed_vs_fp32"] = {"time": f32["solve_s"] / scale["solve_s"],
+                                  "workspace": scale["workspace_gb"] / f32["workspace_gb"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -124,7 +124,10 @@ size_t claire_workspace_bytes(const claire_ctx* ctx);
 claire_status claire_set_images(claire_ctx* ctx, const float* m0, const float* m1);
 
 /* m(1) of the state equation (eq. transport, Sec. 2.2) for velocity v:
- * RK2 departure points (Sec. 2.5.2) and nt homogeneous SL steps. */
+ * RK2 departure points (Sec. 2.5.2) and nt homogeneous SL steps.  In the mixed
+ * form (options.precision = 1) the state between the steps is stored in FP16
+ * with the images' power-of-two scale, as in the solver; m1_out is FP32.  The
+ * state history of the last evaluation is left untouched. */
 claire_status claire_transport(claire_ctx* ctx, const float* v, float* m1_out);
 
 /* Objective J (eq. varopt-claire) and reduced gradient g (eq. rgrad, plus the

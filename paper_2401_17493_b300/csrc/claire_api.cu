@@ -1549,14 +1549,26 @@ claire_status claire_transport(claire_ctx* c, const float* v, float* m1_out) {
   if (!c || !v || !m1_out) return CLAIRE_EINVAL;
   const int64_t N = N_of(c);
   launch_trace(c->g, v, c->dtrial, nullptr, ht_of(c), c->st);
-  const float* src = c->m0;
-  for (int j = 0; j < c->nt; ++j) {
-    float* dst = (j == c->nt - 1) ? m1_out : ((j % 2 == 0) ? c->pp0 : c->pp1);
-    launch_sl(c->g, src, c->dtrial, nullptr, 1.0f, nullptr, 0.0f, dst, c->st);
-    src = dst;
+  if (mixed(c)) {
+    // the mixed form's own m(1): FP16 storage of sig_m m between the steps (the
+    // work fields of the matvec; the evaluation's histories are left as they are)
+    launch_axpy_h(N, c->sig_m, c->m0, 0.0f, nullptr, c->ph0, c->st);
+    const __half* hsrc = c->ph0;
+    for (int j = 0; j < c->nt; ++j) {
+      __half* hdst = (j % 2 == 0) ? c->ph1 : c->ph0;
+      launch_sl_h(c->g, hsrc, c->dtrial, nullptr, 1.0f, nullptr, 0.0f, hdst, c->st);
+      hsrc = hdst;
+    }
+    launch_h2f(N, 1.0f / c->sig_m, hsrc, m1_out, c->st);
+  } else {
+    const float* src = c->m0;
+    for (int j = 0; j < c->nt; ++j) {
+      float* dst = (j == c->nt - 1) ? m1_out : ((j % 2 == 0) ? c->pp0 : c->pp1);
+      launch_sl(c->g, src, c->dtrial, nullptr, 1.0f, nullptr, 0.0f, dst, c->st);
+      src = dst;
+    }
   }
   TRY(check_launch(c, "transport"));
-  (void)N;
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return CLAIRE_OK;
 }

@@ -122,6 +122,7 @@ bool launch_accum_hist_h(const Grid& g, const __half* lhist, const __half* mhist
                          float* out, const float* dotv, double* partial, cudaStream_t st);
 void launch_axpy_h(int64_t n, float a, const float* x, float b, const __half* z, __half* y,
                    cudaStream_t st);
+void launch_h2f(int64_t n, float a, const __half* x, float* y, cudaStream_t st);
 void launch_sqdiff_h(int64_t n, const __half* m, float a, const float* m1, double* partial,
                      int nblocks, double* out, cudaStream_t st);
 

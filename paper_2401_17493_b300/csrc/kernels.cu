@@ -42,9 +42,10 @@ static dim3 grid3(const Grid& g) {
 // ---------------------------------------------------------------- trace
 
 // RK2 departure points of both directions (Sec. 2.5.2) for a tile of nodes.
-// The velocity components are staged one at a time into one brick; the
-// predictor y~ = x -+ h_t v(x) is interpolated from it, and the corrector
-// y = x -+ (h_t / 2)(v(x) + v(y~)) is stored as y - x in grid units.
+// The velocity components are staged one at a time into one brick, which
+// serves both directions; the predictor y~ = x -+ h_t v(x) is interpolated
+// from it, and the corrector y = x -+ (h_t / 2)(v(x) + v(y~)) is stored as
+// y - x in grid units.
 __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __restrict__ v,
                                                          float* __restrict__ df,
                                                          float* __restrict__ db, float ht,
@@ -56,26 +57,25 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   const bool active = i2 < g.n2 && i3 < g.n3;
   const int kmax = min(t1, g.n1 - i1_0);
-  bool first = true;
+  const int64_t idx0 = active ? lin(g, i1_0, i2, i3) : 0;
 #pragma unroll 1
-  for (int dir = 0; dir < 2; ++dir) {
-    float* out = dir == 0 ? df : db;
-    if (out == nullptr) continue;
-    const float sg = dir == 0 ? -ht : ht;        // transport along +v / -v
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      if (!first) __syncthreads();               // previous brick consumed
-      first = false;
-      // v(x) of the next node is loaded one node ahead (the first while the
-      // brick is being staged)
-      const int64_t idx0 = active ? lin(g, i1_0, i2, i3) : 0;
-      float vn[3];
+  for (int c = 0; c < 3; ++c) {
+    if (c > 0) __syncthreads();                  // previous brick consumed
+    // v(x) of the first node is loaded while the brick is being staged
+    float v0[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) vn[a] = active ? v[a * N + idx0] : 0.f;
-      stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm, t1);
-      __syncthreads();
-      if (!active) continue;
-      const float ihc = c == 0 ? g.inv_h1 : (c == 1 ? g.inv_h2 : g.inv_h3);
+    for (int a = 0; a < 3; ++a) v0[a] = active ? v[a * N + idx0] : 0.f;
+    stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm, t1);
+    __syncthreads();
+    if (!active) continue;
+    const float ihc = c == 0 ? g.inv_h1 : (c == 1 ? g.inv_h2 : g.inv_h3);
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      float* out = dir == 0 ? df : db;
+      if (out == nullptr) continue;
+      const float sg = dir == 0 ? -ht : ht;      // transport along +v / -v
+      // v(x) of the next node is loaded one node ahead
+      float vn[3] = {v0[0], v0[1], v0[2]};
 #pragma unroll 2
       for (int k = 0; k < kmax; ++k) {
         const int64_t idx = idx0 + k * s1;

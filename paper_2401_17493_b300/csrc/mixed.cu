@@ -214,6 +214,13 @@ __global__ void k_axpy_h(int64_t n, float a, const float* __restrict__ x, float 
   }
 }
 
+// y = a float(x), x in FP16 (a stored field back to FP32, unscaled).
+__global__ void k_h2f(int64_t n, float a, const __half* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * __half2float(x[i]);
+}
+
 // partial sums of (a m(x) - m1(x))^2 with m in FP16 (objective's distance term).
 __global__ void __launch_bounds__(256) k_sqdiff_h(int64_t n, const __half* __restrict__ m,
                                                   float a, const float* __restrict__ m1,
@@ -291,6 +298,11 @@ void launch_axpy_h(int64_t n, float a, const float* x, float b, const __half* z,
                    cudaStream_t st) {
   ProfileRange pr(K_VECTOR, (double)n * (6 + 2 * (z != nullptr)), st);
   k_axpy_h<<<vector_blocks(n), 256, 0, st>>>(n, a, x, b, z, y);
+}
+
+void launch_h2f(int64_t n, float a, const __half* x, float* y, cudaStream_t st) {
+  ProfileRange pr(K_VECTOR, (double)n * 6, st);
+  k_h2f<<<vector_blocks(n), 256, 0, st>>>(n, a, x, y);
 }
 
 void launch_sqdiff_h(int64_t n, const __half* m, float a, const float* m1, double* partial,

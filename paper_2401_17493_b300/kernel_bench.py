@@ -50,6 +50,7 @@ def main():
     d, _ = ctx.trace(v)
     out1 = torch.empty(shape, device="cuda")
     w = torch.empty((3,) + shape, device="cuda")
+    w2 = torch.empty((3,) + shape, device="cuda")
     vt = torch.from_numpy(synth.bandlimited_velocity(shape, 8, 1.0, 5).astype(np.float32)).cuda()
     ctx.objective_gradient(0.5 * v, want_gradient=False)     # state history for the matvec
     cases = {
@@ -57,6 +58,9 @@ def main():
                                              claire._ptr(out1)), 20 * N),
         "trace": (lambda: ctx.lib.claire_trace(ctx.h, claire._ptr(v), claire._ptr(w), None),
                   24 * N),
+        # both directions (forward and backward departure points) in one launch
+        "trace2": (lambda: ctx.lib.claire_trace(ctx.h, claire._ptr(v), claire._ptr(w),
+                                                claire._ptr(w2)), 36 * N),
         "grad8": (lambda: ctx.lib.claire_grad8(ctx.h, claire._ptr(u), claire._ptr(w)), 16 * N),
         "div8": (lambda: ctx.lib.claire_div8(ctx.h, claire._ptr(v), claire._ptr(out1)), 16 * N),
         # one Gauss-Newton matvec: sdot_hist, 8 SL steps, accum_hist, spectral, cufft
@@ -67,7 +71,7 @@ def main():
         "precond": (lambda: ctx.lib.claire_precondition(ctx.h, claire._ptr(vt), claire._ptr(w),
                                                         None), None),
     }
-    kind = {"sl": "sl_step", "trace": "trace", "grad8": "grad8", "div8": "div8",
+    kind = {"sl": "sl_step", "trace": "trace", "trace2": "trace", "grad8": "grad8", "div8": "div8",
             "matvec": None, "precond": None}
     res = {}
     for name, (fn, nbytes) in cases.items():

@@ -519,6 +519,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--beta", type=float, default=1e-2)
     ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--batch", type=int, default=4, help="training samples per Adam step")
+    ap.add_argument("--warmup", type=int, default=250, help="linear learning-rate warm-up steps")
     ap.add_argument("--precond", type=int, default=PRECOND,
                     help="registration preconditioner: 0 spectral, 1 two-level")
     ap.add_argument("--combined-batch", default="16",
@@ -547,7 +549,8 @@ def main():
     model = UNet3D(seed=0)
     log(f"U-Net parameters: {model.parameters}")
     t0 = time.perf_counter()
-    hist = train(model, inputs, targets, args.epochs, lr=args.lr, log=log)
+    hist = train(model, inputs, targets, args.epochs, lr=args.lr, batch=args.batch, log=log,
+                 warmup=args.warmup)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     res = evaluate(model, make_pairs(eval_seeds, n), n, args.beta)

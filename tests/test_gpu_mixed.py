@@ -48,6 +48,25 @@ def claire():
 
 
 @pytest.mark.parametrize("shape", [RAGGED, CUBE])
+def test_mixed_transport_error(claire, shape):
+    """m(1) with FP16 storage between the SL steps against the FP64 oracle's m(1):
+    n_t roundings of the stored state (2^-11 relative each) plus the FP32 path."""
+    from oracle import transport as OT
+    m0, m1, vtrue = synth.blob_pair(shape, seed=1)
+    v = 0.8 * vtrue
+    ref = OT.state_solve(f64(m0), f64(v), 4)[-1]
+    with claire.Context(shape, nt=4, beta_v=1e-2, precision=1) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        m_mixed = host(ctx.transport(dev(v)))
+        ctx.set_options(precision=0)
+        m_fp32 = host(ctx.transport(dev(v)))
+    e_mixed, e_fp32 = rel(m_mixed, ref), rel(m_fp32, ref)
+    print(f"mixed {shape}: m(1) {e_mixed:.2e} (FP32 storage {e_fp32:.2e})")
+    assert e_fp32 < 1e-5
+    assert 1e-6 < e_mixed < 1e-3
+
+
+@pytest.mark.parametrize("shape", [RAGGED, CUBE])
 def test_mixed_objective_gradient_and_matvec_errors(claire, shape):
     m0, m1, vtrue = synth.blob_pair(shape, seed=1)
     v = 0.4 * vtrue
