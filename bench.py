@@ -232,6 +232,8 @@ def run_batch(args, pairs):
     t_batch = time.perf_counter() - t0
     same = all(torch.equal(a, b) for a, b in zip(v_seq, vs))
     voxels = sum(int(np.prod(c.shape)) for c in ctxs)
+    # PDE solves x voxels: the transport work of the batch, comparable across grid sizes
+    vox_pde = sum(int(np.prod(c.shape)) * st.pde_solves for c, st in zip(ctxs, bstats))
     for c in ctxs:
         c.close()
     return {"pairs": len(ctxs), "grids": sorted(set(str(c) for c, _, _ in pairs)),
@@ -240,6 +242,8 @@ def run_batch(args, pairs):
             "matvecs": int(sum(st.matvecs for st in bstats)),
             "all_converged": all(st.grad_rel <= EPS_OPT for st in bstats),
             "batched_equals_sequential": bool(same),
+            "voxel_pde_solves": vox_pde,
+            "voxel_pde_solves_per_s": {"batched": vox_pde / t_batch, "sequential": vox_pde / t_seq},
             "workload": "ellipsoid phantom pairs seeds 1000.., grids from {64^3, 96x112x80, "
                         "128^3, 160x192x144, 192^3}, beta_v 5e-3, nt 4, rel-grad 5e-2, "
                         "two-level preconditioner"}
@@ -673,6 +677,8 @@ def run_claire(args, world, rank, local):
     torch.cuda.empty_cache()
 
     batch = run_batch(args, pairs) if pairs is not None else None
+    if batch is not None:           # the same rate of one 256^3 registration, for comparison
+        batch["voxel_pde_solves_per_s"]["single_large_solve"] = st0["pde_solves"] * n ** 3 / s_per_solve
     combined = None
     if rank == 0 and world == 1 and not args.no_combined:
         combined = run_combined(args)

@@ -122,3 +122,20 @@ def test_tuning_rejects_unknown_shapes(claire):
             with pytest.raises(claire.ClaireError):
                 ctx.set_tuning(*bad)
         assert ctx.tuning() == (0, 8, 32)
+
+
+def test_tuning_change_after_graph_capture_gives_the_same_solve(claire):
+    """Captured PCG graphs bake the launch shapes: set_tuning drops them, and the
+    next solve (re-captured with the new shapes) is bitwise the first one."""
+    shape = (32, 32, 32)
+    m0, m1, _ = synth.blob_pair(shape, seed=6, kmax=3, max_disp_voxels=2.0)
+    with claire.Context(shape, nt=4, beta_v=1e-2, precond=1, max_inner=10, graphs=1) as ctx:
+        ctx.set_images(dev(m0), dev(m1))
+        v1, s1 = ctx.solve()
+        v1 = v1.clone()
+        ctx.set_tuning(1, 4, 16)
+        v2, s2 = ctx.solve()
+        ctx.set_tuning(0, 16, 64)
+        v3, s3 = ctx.solve()
+    assert torch.equal(v1, v2) and torch.equal(v1, v3)
+    assert s1.matvecs == s2.matvecs == s3.matvecs
