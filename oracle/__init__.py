@@ -29,7 +29,10 @@ Parity pins (tests/test_oracle_*.py) tie every module to something other than
 itself: closed forms, the v = 0 special case the paper works out, textbook
 library routines, brute force on tiny inputs and invariants.  The
 near-incompressible weight c(kappa) of ``spectral.near_incompressible_term``
-is only checked through its limits: parity unpinned for that one function.
+is pinned to the meaning of the Appendix's printed operator: the gradient it
+gives vanishes at the minimiser of the constrained problem that operator
+comes from (computed independently); which regulariser of the second control
+the paper intended stays reading C-2.
 """
 
 from . import grid, interp, fd8, spectral, transport, reduced, precond, solver, defgrad  # noqa: F401

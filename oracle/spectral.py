@@ -100,8 +100,10 @@ def near_incompressible_weight(shape, alpha, beta_w):
 
     Reading C-2 of the Appendix's garbled near-incompressible gradient
     grad (alpha (beta (-Lap^-1 + id))^-1 + id)^-1 Lap^-1 div, with kappa = |k|^2.
-    beta_w -> infinity gives 1 (full Leray), beta_w = 0 gives 0.
-    Parity unpinned beyond those limits.
+    beta_w -> infinity gives 1 (full Leray), beta_w = 0 gives 0.  The printed
+    operator is (beta B)(alpha + beta B)^-1 with B = -Lap^-1 + id: the weight of
+    the gradient obtained by eliminating div v = w and its dual variable from a
+    problem whose second control w is regularised by (beta / 2) <w, B w>.
     """
     kap = kappa(shape)
     num = beta_w * (1.0 + kap)
