@@ -123,24 +123,24 @@ __device__ __forceinline__ float2 window_plane_sum(const WinPlane& q, const Node
 }
 
 // Append every lane's queued nodes (bit k of `mask`: node k of the lane's
-// column) to the CTA queue as codes k << 8 | ty << 5 | lane: one shared-memory
+// column, k < kmax <= 16) to the CTA queue as codes k << 8 | ty << 5 | lane,
+// ordered by node row k and then by lane (consecutive queue entries then sit
+// in different lanes, so the deferred gather's warps hit fewer shared-memory
+// banks twice than with each lane's nodes stored together); one shared-memory
 // atomic per warp.  Every lane of the warp must call it.
-__device__ __forceinline__ void window_enqueue(unsigned mask, int ty, int lane,
+__device__ __forceinline__ void window_enqueue(unsigned mask, int kmax, int ty, int lane,
                                                int* __restrict__ queue, int* __restrict__ qcount) {
-  const int cnt = __popc(mask);
-  int incl = cnt;                                   // inclusive prefix over the lanes
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += x;
-  }
+  const unsigned below = (1u << lane) - 1u;
+  int total = 0;
+  for (int k = 0; k < kmax; ++k) total += __popc(__ballot_sync(0xffffffffu, (mask >> k) & 1u));
+  if (total == 0) return;
   int base = 0;
-  if (lane == 31 && incl > 0) base = atomicAdd(qcount, incl);
-  base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
-  while (mask) {
-    const int k = __ffs(mask) - 1;
-    mask &= mask - 1u;
-    queue[base++] = (k << 8) | (ty << 5) | lane;
+  if (lane == 0) base = atomicAdd(qcount, total);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int k = 0; k < kmax; ++k) {
+    const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1u);
+    if ((mask >> k) & 1u) queue[base + __popc(m & below)] = (k << 8) | (ty << 5) | lane;
+    base += __popc(m);
   }
 }
 
@@ -194,7 +194,7 @@ __device__ __forceinline__ void window_march(const float* __restrict__ s, int km
     CLAIRE_WIN_STEP(3, w3, w0, w1, w2)
   }
 #undef CLAIRE_WIN_STEP
-  window_enqueue(slow, ty, lane, queue, qcount);
+  window_enqueue(slow, kmax, ty, lane, queue, qcount);
 }
 
 // Gather the queued nodes with all threads of the CTA (call after a barrier
