@@ -1103,8 +1103,9 @@ claire_status absmax3(claire_ctx* c, const float* a, double* out) {
 
 // Autotuner: time each compiled tile shape on this context's own grid and
 // buffers (the state history and departure points of the current evaluation)
-// with CUDA events, keep the fastest.  Brick depth along x1 for the SL steps
-// (4, 8, 16), planes per CTA for the FD8 history kernels (8, 16, 32, 64).
+// with CUDA events, keep the fastest.  For the SL steps both gather variants
+// (64 shared loads per node, register window) at brick depths 4, 8, 16 along
+// x1; planes per CTA for the FD8 history kernels (8, 16, 32, 64).
 claire_status autotune(claire_ctx* c) {
   if (!c->have_eval) return fail(c, CLAIRE_EORDER, "autotune needs an evaluated state");
   const int64_t N = N_of(c);
