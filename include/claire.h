@@ -356,9 +356,13 @@ claire_status claire_conv3d_wgrad(const void* x, int B, int D, int H, int W, int
  *  7      b += a (V x C elements) */
 claire_status claire_unet_op(int op, const void* a, void* b, long long V, int C, int Cdst,
                              int c_off, int B, int D, int H, int W, void* stream);
-/* db[c] = sum_v dy[v][c] (FP32, fixed order). */
+/* db[c] = sum_v dy[v][c] (FP32 result of a fixed-order FP64 sum: up to nblocks
+ * CTAs each sum a contiguous range of voxels for every channel into partial
+ * (caller-owned device scratch of nblocks x C doubles), then the partials are
+ * added in CTA order).  dy 4-byte aligned, C even and <= 512, nblocks >= 1;
+ * EINVAL otherwise. */
 claire_status claire_unet_bias_grad(const void* dy, long long V, int C, float* db,
-                                    void* stream);
+                                    double* partial, int nblocks, void* stream);
 /* out[v][c] = BF16(scale * f[c][v]) for c < nf, 0 for nf <= c < C. */
 claire_status claire_unet_pack(long long V, int nf, const float* f, float scale, int C,
                                void* out, void* stream);

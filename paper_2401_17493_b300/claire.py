@@ -123,7 +123,7 @@ def load_library(path=LIB_PATH):
         "claire_conv3d_flip_weights": ([P, I, I, P, P], I),
         "claire_conv3d_wgrad": ([P, I, I, I, I, I, P, I, P, I, P, P], I),
         "claire_unet_op": ([I, P, P, ctypes.c_longlong, I, I, I, I, I, I, I, P], I),
-        "claire_unet_bias_grad": ([P, ctypes.c_longlong, I, P, P], I),
+        "claire_unet_bias_grad": ([P, ctypes.c_longlong, I, P, P, I, P], I),
         "claire_unet_pack": ([ctypes.c_longlong, I, P, ctypes.c_float, I, P, P], I),
         "claire_unet_mse": ([ctypes.c_longlong, I, P, P, ctypes.c_float, P, P, P, I, P, P], I),
         "claire_unet_adam": ([ctypes.c_longlong, P, P, P, P, ctypes.c_float, ctypes.c_float,

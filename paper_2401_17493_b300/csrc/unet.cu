@@ -607,14 +607,52 @@ __global__ void k_sum_partials(const float* __restrict__ part, int nsplit, int64
   out[i] = acc;
 }
 
-// db[n] = sum_v dY[v][n] (deterministic two-level sum per channel)
-__global__ void __launch_bounds__(256) k_bias_grad(const bf16* __restrict__ dY, int64_t V, int C,
-                                                   float* __restrict__ db) {
-  const int n = blockIdx.x;
-  KahanF acc;
-  for (int64_t v = threadIdx.x; v < V; v += blockDim.x) acc.add(__bfloat162float(dY[v * C + n]));
-  const double b = block_sum(acc.value());
-  if (threadIdx.x == 0) db[n] = (float)b;
+// Bias gradient db[c] = sum_v dY[v][c] in two deterministic stages.
+// Stage 1: CTA b sums the voxels [b chunk, (b + 1) chunk) for every channel:
+// thread t takes the channel pair (2 p, 2 p + 1), p = t % (C / 2), of every
+// (256 / (C / 2))-th voxel from t / (C / 2) on (bf16x2 loads, a warp reads
+// whole voxel rows), compensated FP32 per thread, then the threads of a pair
+// are added in a fixed order in FP64 into part[b][c].
+__global__ void __launch_bounds__(256) k_bias_grad_part(const bf16* __restrict__ dY, int64_t V,
+                                                        int C, int64_t chunk,
+                                                        double* __restrict__ part) {
+  __shared__ double red[256][2];
+  const int P = C >> 1, t = threadIdx.x;
+  const int rows = 256 / P;
+  const int p = t % P, r = t / P;
+  const int64_t v0 = (int64_t)blockIdx.x * chunk;
+  const int64_t v1 = v0 + chunk < V ? v0 + chunk : V;
+  KahanF a0, a1;
+  if (r < rows) {
+#pragma unroll 4
+    for (int64_t v = v0 + r; v < v1; v += rows) {
+      const __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162*>(dY + v * C + 2 * p);
+      a0.add(__low2float(x));
+      a1.add(__high2float(x));
+    }
+  }
+  red[t][0] = a0.value();
+  red[t][1] = a1.value();
+  __syncthreads();
+  if (t < P) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q < rows; ++q) {
+      s0 += red[q * P + t][0];
+      s1 += red[q * P + t][1];
+    }
+    part[(int64_t)blockIdx.x * C + 2 * t] = s0;
+    part[(int64_t)blockIdx.x * C + 2 * t + 1] = s1;
+  }
+}
+
+// Stage 2: db[c] = sum over the CTAs of part[b][c], in CTA order.
+__global__ void k_bias_grad_final(const double* __restrict__ part, int nblocks, int C,
+                                  float* __restrict__ db) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * C + c];
+  db[c] = (float)s;
 }
 
 // ------------------------------------------------------------------ layer ops
@@ -1223,8 +1261,15 @@ claire_status claire_unet_op(int op, const void* a, void* b, long long V, int C,
 }
 
 claire_status claire_unet_bias_grad(const void* dy, long long V, int C, float* db,
-                                    void* stream) {
-  k_bias_grad<<<C, 256, 0, (cudaStream_t)stream>>>((const bf16*)dy, V, C, db);
+                                    double* partial, int nblocks, void* stream) {
+  if (!dy || !db || !partial || V < 1 || nblocks < 1 || C < 2 || C % 2 || C > 512 ||
+      (reinterpret_cast<uintptr_t>(dy) & 3))
+    return CLAIRE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t chunk = (V + nblocks - 1) / nblocks;
+  const int nb = (int)((V + chunk - 1) / chunk);           // CTAs that own voxels
+  k_bias_grad_part<<<nb, 256, 0, st>>>((const bf16*)dy, V, C, chunk, partial);
+  k_bias_grad_final<<<(C + 255) / 256, 256, 0, st>>>(partial, nb, C, db);
   return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
 }
 

@@ -55,6 +55,9 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+BIAS_BLOCKS = 592           # CTAs of the bias-gradient reduction (4 per SM of a B300)
+
+
 def _check(st, what):
     if st != C.OK:
         raise C.ClaireError(st, what)
@@ -86,9 +89,11 @@ class Conv:
             _p(y), _p(y32), _stream()), "conv3d_forward")
         return y
 
-    def backward(self, x, y, dy, vol, need_dx=True, partial=None):
+    def backward(self, x, y, dy, vol, need_dx=True, partial=None, bias_part=None):
         """dy: gradient w.r.t. this layer's (post-activation) output, BF16 [V][cout]
-        (overwritten); accumulates nothing: sets dw, db; returns dx or None."""
+        (overwritten); accumulates nothing: sets dw, db; returns dx or None.
+        partial: scratch of the weight gradient; bias_part: FP64 scratch of the
+        bias gradient (BIAS_BLOCKS x cout doubles)."""
         import torch
         L = C.load_library()
         V = vol[0] * vol[1] * vol[2] * vol[3]
@@ -102,7 +107,10 @@ class Conv:
             raise ValueError("wgrad partial buffer too small")
         _check(L.claire_conv3d_wgrad(_p(x), *vol, self.cin, _p(dy), self.cout, _p(partial),
                                      nsplit, _p(self.dw), s), "wgrad")
-        _check(L.claire_unet_bias_grad(_p(dy), V, self.cout, _p(self.db), s), "bias_grad")
+        if bias_part is None or bias_part.numel() < BIAS_BLOCKS * self.cout:
+            raise ValueError("bias-gradient scratch buffer too small")
+        _check(L.claire_unet_bias_grad(_p(dy), V, self.cout, _p(self.db), _p(bias_part),
+                                       BIAS_BLOCKS, s), "bias_grad")
         if not need_dx:
             return None
         _check(L.claire_conv3d_flip_weights(_p(self.w), self.cout, self.cin, _p(self.wf), s),
@@ -151,6 +159,7 @@ class UNet3D:
         self.step_count = 0
         self.partial = None
         self.wpart = None
+        self.bpart = None           # FP64 scratch of the bias gradients
 
     @property
     def parameters(self):
@@ -232,9 +241,14 @@ class UNet3D:
         if self.wpart is None or self.wpart.numel() < need:
             self.wpart = torch.empty(need, device="cuda")
         wp = self.wpart
+        if self.bpart is None:
+            self.bpart = torch.empty(BIAS_BLOCKS * max(l.cout for l in L.values()),
+                                     device="cuda", dtype=torch.float64)
+        bp = self.bpart
 
         def bwd(name, x, y, dy, lvl, need_dx=True):
-            return L[name].backward(x, y, dy, vols[lvl], need_dx=need_dx, partial=wp)
+            return L[name].backward(x, y, dy, vols[lvl], need_dx=need_dx, partial=wp,
+                                    bias_part=bp)
 
         def split(gcat, lvl, ca, cs):
             """d(concat(up(coarse), skip)) -> (d coarse, d skip)."""
@@ -327,10 +341,37 @@ def solve_targets(pairs, n, beta, eps_opt=5e-2, batch=8):
     return out
 
 
-def train(model, inputs, targets, epochs, lr=5e-4, batch=4, seed=0, log=None, warmup=250):
+def symmetry(fields, target, g):
+    """Element g (0..47) of the cube's symmetry group applied to a training
+    sample: the axes are permuted (g // 8 indexes the 6 permutations) and
+    flipped (bits of g % 8).  The registration problem is covariant under it
+    (L = -Lap and the L2 distance are invariant; transport commutes with it),
+    so the relabelled pair has the relabelled velocity: components permuted
+    with the axes and negated along flipped axes.  torch.flip maps index i to
+    n - 1 - i, a reflection composed with a one-voxel shift, which the periodic
+    problem also commutes with."""
+    import itertools
+    perm = list(itertools.permutations(range(3)))[g // 8]
+    flips = [d for d in range(3) if (g % 8) >> d & 1]
+    sp = (0, 1 + perm[0], 1 + perm[1], 1 + perm[2])
+    f = fields.permute(*sp)
+    t = target[list(perm)].permute(*sp)
+    if flips:
+        f = f.flip([1 + d for d in flips])
+        t = t.flip([1 + d for d in flips])
+        sign = t.new_ones(3)
+        sign[flips] = -1.0
+        t = t * sign.reshape(3, 1, 1, 1)
+    return f.contiguous(), t.contiguous()
+
+
+def train(model, inputs, targets, epochs, lr=5e-4, batch=4, seed=0, log=None, warmup=250,
+          augment=False):
     """Adam with a linear warm-up over the first `warmup` steps, then a cosine
     decay per epoch (the warm-up keeps the first large Adam steps from
-    silencing the ReLUs, which left the loss at the zero-prediction plateau)."""
+    silencing the ReLUs, which left the loss at the zero-prediction plateau).
+    With augment, every sample of every step is relabelled by a random element
+    of the cube's symmetry group (`symmetry`)."""
     import torch
     rng = np.random.default_rng(seed)
     n_in = len(inputs)
@@ -343,8 +384,14 @@ def train(model, inputs, targets, epochs, lr=5e-4, batch=4, seed=0, log=None, wa
         lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / max(1, epochs)))
         for i in range(0, n_in - batch + 1, batch):
             idx = order[i:i + batch]
-            fields = [inputs[j] for j in idx]
-            tgt = torch.cat([targets[j].reshape(3, 1, -1) for j in idx], dim=1).reshape(3, -1)
+            if augment:
+                pairs = [symmetry(inputs[j], targets[j], int(rng.integers(0, 48))) for j in idx]
+                fields = [p[0] for p in pairs]
+                tgts = [p[1] for p in pairs]
+            else:
+                fields = [inputs[j] for j in idx]
+                tgts = [targets[j] for j in idx]
+            tgt = torch.cat([t.reshape(3, 1, -1) for t in tgts], dim=1).reshape(3, -1)
             out = model.forward(fields, len(idx))
             loss = model.loss_and_backward(out, (tgt / V_SCALE).contiguous())  # network units
             step += 1
@@ -429,9 +476,9 @@ def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
     Both arms stop at the same relative gradient with the same denominator
     |g(0)|_inf (from an FP32 evaluation at v = 0).  Context creation, one untimed
     set-up solve and g(0) are outside both timings; both arms reuse their contexts
-    (set_images per pair: one for the plain arm, `batch` for the combined one), and
-    the combined time is the wall time from the first prediction to the last
-    solve."""
+    and load each pair's images (set_images) inside their timings (one context for
+    the plain arm, `batch` for the combined one), and the combined time is the
+    wall time from the first prediction to the last solve."""
     import torch
     opts = dict(nt=4, beta_v=beta, eps_opt=eps_opt, precond=PRECOND, max_inner=MAX_INNER)
     res = {k: [] for k in ("matvecs_plain", "matvecs_combined", "mismatch_plain",
@@ -443,14 +490,17 @@ def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
     with C.Context((n, n, n), **opts) as cp:
         cp.set_images(*pairs[0])
         cp.solve(zeros())
-        for (m0, m1) in pairs:
+        for (m0, m1) in pairs:                       # the denominators, untimed
             cp.set_images(m0, m1)
             _, g0 = cp.objective_gradient(zeros())
             gnorm0s.append(float(g0.abs().max()))
-            cp.set_options(gnorm0=gnorm0s[-1])
+        for (m0, m1), gn0 in zip(pairs, gnorm0s):
+            v0 = zeros()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, st = cp.solve(zeros())
+            cp.set_images(m0, m1)
+            cp.set_options(gnorm0=gn0)
+            _, st = cp.solve(v0)
             torch.cuda.synchronize()
             t_plain += time.perf_counter() - t0
             res["matvecs_plain"].append(st.matvecs)
@@ -521,6 +571,8 @@ def main():
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--batch", type=int, default=4, help="training samples per Adam step")
     ap.add_argument("--warmup", type=int, default=250, help="linear learning-rate warm-up steps")
+    ap.add_argument("--augment", type=int, default=0, choices=[0, 1],
+                    help="relabel training samples by random symmetries of the cube")
     ap.add_argument("--precond", type=int, default=PRECOND,
                     help="registration preconditioner: 0 spectral, 1 two-level")
     ap.add_argument("--combined-batch", default="16",
@@ -550,7 +602,7 @@ def main():
     log(f"U-Net parameters: {model.parameters}")
     t0 = time.perf_counter()
     hist = train(model, inputs, targets, args.epochs, lr=args.lr, batch=args.batch, log=log,
-                 warmup=args.warmup)
+                 warmup=args.warmup, augment=bool(args.augment))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     res = evaluate(model, make_pairs(eval_seeds, n), n, args.beta)

@@ -277,3 +277,29 @@ def test_a_few_training_steps_lower_the_loss(lib):
         losses.append(float(model.loss_and_backward(out, tgt)))
         model.step(1e-3)
     assert losses[-1] < 0.8 * losses[0]
+
+
+@pytest.mark.parametrize("V,C", [(1, 16), (1000, 16), (262147, 32), (70001, 128), (5003, 512)])
+def test_bias_gradient_matches_a_float64_sum(lib, V, C):
+    """db[c] = sum_v dy[v][c] for ragged voxel counts, several channel counts and
+    fewer voxels than reduction CTAs; invalid arguments are refused."""
+    from paper_2401_17493_b300 import claire as C_
+    L = C_.load_library()
+    gen = torch.Generator(device="cuda").manual_seed(V + C)
+    dy = torch.randn((V, C), device="cuda", generator=gen).to(torch.bfloat16)
+    db = torch.empty(C, device="cuda")
+    part = torch.empty(592 * C, device="cuda", dtype=torch.float64)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.claire_unet_bias_grad(ctypes.c_void_p(dy.data_ptr()), V, C,
+                                   ctypes.c_void_p(db.data_ptr()),
+                                   ctypes.c_void_p(part.data_ptr()), 592, st) == C_.OK
+    ref = dy.double().sum(0)
+    err = (db.double() - ref).abs().max().item() / max(1.0, ref.abs().max().item())
+    assert err < 1e-6
+    # odd channel counts, too many channels, no scratch
+    for bad in [(C + 1, 592, part), (514, 592, part), (C, 592, None), (C, 0, part)]:
+        c_, nb, p = bad
+        assert L.claire_unet_bias_grad(ctypes.c_void_p(dy.data_ptr()), V, c_,
+                                       ctypes.c_void_p(db.data_ptr()),
+                                       None if p is None else ctypes.c_void_p(p.data_ptr()),
+                                       nb, st) == C_.EINVAL
