@@ -358,8 +358,8 @@ claire_status claire_unet_op(int op, const void* a, void* b, long long V, int C,
                              int c_off, int B, int D, int H, int W, void* stream);
 /* db[c] = sum_v dy[v][c] (FP32 result of a fixed-order FP64 sum: up to nblocks
  * CTAs each sum a contiguous range of voxels for every channel into partial
- * (caller-owned device scratch of nblocks x C doubles), then the partials are
- * added in CTA order).  dy 4-byte aligned, C even and <= 512, nblocks >= 1;
+ * (caller-owned device scratch of nblocks x C doubles), then the partials of a
+ * channel are added in a fixed order).  dy 4-byte aligned, C even and <= 512, nblocks >= 1;
  * EINVAL otherwise. */
 claire_status claire_unet_bias_grad(const void* dy, long long V, int C, float* db,
                                     double* partial, int nblocks, void* stream);

@@ -9,6 +9,12 @@ prints one JSON line per layer: microseconds, TFLOP/s (2 V Cout 27 Cin per
 launch) and the minimum-traffic rate (each activation read once, each output
 written once).  With a layer name only that layer runs (the command profiled
 by ncu for the convolution captures).
+
+    python -m paper_2401_17493_b300.conv_bench steps [n]
+
+times n (default 8) whole training steps of the U-Net (forward, loss,
+backward, Adam) at batch 4 on random 64^3 inputs and targets, after one
+untimed epoch of 4 steps (the command profiled for the training launch list).
 """
 
 import ctypes
@@ -24,12 +30,34 @@ LAYERS = [("e0b", 64, 16, 16), ("d0a", 64, 48, 16), ("e1b", 32, 32, 32), ("d1a",
 BATCH = 4
 
 
+def train_steps(n):
+    import time
+    import torch
+    from paper_2401_17493_b300 import unet as U
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    inputs = [torch.rand((2, 64, 64, 64), device="cuda", generator=gen) for _ in range(16)]
+    targets = [0.01 * torch.randn((3, 64, 64, 64), device="cuda", generator=gen)
+               for _ in range(16)]
+    model = U.UNet3D(seed=0)
+    U.train(model, inputs, targets, 1, batch=BATCH)         # 4 untimed steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    U.train(model, inputs, targets, max(1, n // 4), batch=BATCH)
+    torch.cuda.synchronize()
+    steps = 4 * max(1, n // 4)
+    print(json.dumps({"training_steps": steps, "batch": BATCH,
+                      "ms_per_step": (time.perf_counter() - t0) / steps * 1e3}), flush=True)
+
+
 def main():
     import torch
     from paper_2401_17493_b300 import build, claire as C
     build.build()
     L = C.load_library()
     only = sys.argv[1] if len(sys.argv) > 1 else None
+    if only == "steps":
+        train_steps(int(sys.argv[2]) if len(sys.argv) > 2 else 8)
+        return
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
     gen = torch.Generator(device="cuda").manual_seed(0)

@@ -27,6 +27,15 @@ __device__ __forceinline__ uint64_t umma_smem_desc(const void* p, uint32_t lbo, 
          (1ull << 46);
 }
 
+// The descriptor of p + bytes from the descriptor of p: the start address sits
+// in the low 14 bits in 16-byte units, and a CTA's shared-memory offsets stay
+// below 2^18 bytes, so for a 16-byte multiple the field just grows by bytes / 16
+// (no carry into the other fields).  One add instead of rebuilding the
+// descriptor for every MMA of an issue loop.
+__device__ __forceinline__ uint64_t umma_desc_advance(uint64_t desc, uint32_t bytes) {
+  return desc + (uint64_t)(bytes >> 4);
+}
+
 // Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |

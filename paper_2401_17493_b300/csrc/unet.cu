@@ -302,20 +302,25 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, 
 // Weight gradient on the tensor cores (tcgen05) for volumes with W % 8 == 0,
 // H % 16 == 0 and cin <= cout <= 128, one group of 16 input channels per blockIdx.y:
 //   dW[co][t][ci] = sum_v dY[v][co] X[v + off(t)][ci]
-// as D[co][(t, ci)] += A[co][v] B_t[ci][v] with M = 128 (co, rows >= Cout zero),
-// N = 16, K = voxels.  A persistent CTA walks 8 x 16-voxel tiles of one (sample, z)
+// as D[co][(t, ci)] += A[co][v] B_t[ci][v] with M = 128 (co, rows >= Cout zero) and
+// K = voxels.  A persistent CTA walks 8 x 16-voxel tiles of one (sample, z)
 // (the tiles blockIdx.x, blockIdx.x + gridDim.x, ...), accumulating all 27 taps in
 // 432 TMEM columns.  Per tile it stages A = dY transposed, [y][co][x] x 2 bytes
 // (K-major: 8-voxel x runs are the 16-byte K rows), and the input neighbourhood
 // transposed once per x shift, XT[dx][z'][y'][ci][x] (so every tap's B operand is
-// 16-byte aligned); one thread issues 27 taps x 8 MMAs (K = 16: two y rows each)
-// while the CTA stages the next tile into the other of two buffers.  The CTA's
-// partial dW goes to part[blockIdx.x]; k_sum_partials adds them in order.  Every
-// wait is bounded; a timed-out one makes the CTA's partial NaN.
-// A: 16 y x (128 co x 8 x + 16 bytes): the padding of the y pitch (the leading byte
-// offset) and of the XT block pitch spreads the staging stores over all banks
+// 16-byte aligned).  The transposes run in registers on 8 x 8 blocks (movmatrix):
+// a warp loads 8 voxels x 8 channels, 4 bytes a lane, and stores 8 channel rows of
+// 8 voxels as one 128-byte run, so the staging stores meet no bank conflicts.  With
+// an XT block pitch of 256 bytes the three y shifts of one (dz, dx) pair are
+// consecutive 128-byte groups of B rows, so one MMA with N = 48 (dy, ci) covers
+// them: one thread issues 9 x 8 MMAs (K = 16: two y rows each) per tile while the
+// CTA stages the next tile into the other of two buffers.  TMEM column
+// (dz 3 + dx) 48 + dy 16 + ci holds tap (dz, dy, dx).  The CTA's partial dW goes to
+// part[blockIdx.x]; k_sum_partials adds them in order.  Every wait is bounded; a
+// timed-out one makes the CTA's partial NaN.
+// A: 16 y x (128 co x 8 x + 16 bytes) (the leading byte offset of A is the y pitch)
 constexpr int WG_AP = 128 * 16 + 16;                      // 2064 bytes per y
-constexpr int WG_XP = 16 * 16 + 16;                       // 272 bytes per (dx, z, y) block
+constexpr int WG_XP = 16 * 16;                            // 256 bytes per (dx, z, y) block
 constexpr int WG_A = 16 * WG_AP;
 constexpr int WG_XT = 3 * 3 * 18 * WG_XP;                 // XT: 3 dx x 3 z x 18 y blocks
 constexpr int WG_BUF = WG_A + WG_XT;                      // one tile's operands
@@ -323,9 +328,21 @@ constexpr int WG_BUF = WG_A + WG_XT;                      // one tile's operands
 // TMEM columns) runs per SM
 constexpr int WG_SMEM = 2 * WG_BUF;
 static_assert(WG_SMEM > 114 * 1024 && WG_SMEM <= 227 * 1024, "weight-gradient buffers");
+static_assert(WG_AP % 16 == 0 && WG_XP == 2 * 128 && WG_BUF % 16 == 0,
+              "operand offsets in 16-byte units; XT blocks two 8-row groups apart");
 // 512 threads: more global loads in flight while a tile is staged (transposed)
-// than with 256 (64^3 16 -> 16: 464 vs 499 us; 48 -> 16 transposed: 746 vs 861 us)
+// than with 256
 constexpr int WG_THREADS = 512;
+
+// 8 x 8 transpose of 16-bit elements across a warp: lane l holds row l / 4,
+// columns 2 (l % 4) and 2 (l % 4) + 1 of the source (low half first) and
+// receives the same positions of the transpose.
+__device__ __forceinline__ uint32_t movm_trans(uint32_t a) {
+  uint32_t d;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;\n" : "=r"(d) : "r"(a));
+  return d;
+}
+
 __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __restrict__ X, Vol s,
                                                               int Cin,
                                                               const bf16* __restrict__ dY,
@@ -334,7 +351,7 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __rest
   extern __shared__ __align__(128) uint8_t wg_smem[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = blockIdx.y;                                  // input channels 16 g .. 16 g + 15
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
@@ -351,10 +368,12 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __rest
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = tmem_base;
-  constexpr uint32_t idesc = umma_idesc_bf16(CONV_M, 16);
+  constexpr uint32_t idesc = umma_idesc_bf16(CONV_M, 48);
+  constexpr int NWARPS = WG_THREADS / 32;
   const int xb = s.W / 8, yb = s.H / 16;
   const int ntiles = s.B * s.D * yb * xb;
-  // the operands of tile q into buffer buf
+  const int xr = lane >> 2, cp = 2 * (lane & 3);             // a lane's place in an 8 x 8 block
+  // the operands of tile q into buffer buf (warp-uniform loops: movmatrix)
   auto stage = [&](int q, int buf) {
     uint8_t* A = wg_smem + buf * WG_BUF;
     uint8_t* XT = A + WG_A;
@@ -363,35 +382,29 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __rest
     const int y0 = (q % yb) * 16;
     q /= yb;
     const int z = q % s.D, b = q / s.D;
-    // A[y][co][x] = dY[(x0 + x, y0 + y)][co]; a warp's lanes take 8 x by 4 y
+    // A[y][co][x] = dY[(x0 + x, y0 + y)][co]: blocks of (8 x) x (8 co)
+    const int na = 16 * (Cout / 8);
 #pragma unroll 2
-    for (int i = tid; i < 128 * (Cout / 8); i += WG_THREADS) {
-      const int vl = i & 127, c8 = i >> 7;
-      const int y = vl >> 3, x = vl & 7;
-      const int64_t v = ((int64_t)(b * s.D + z) * s.H + y0 + y) * s.W + x0 + x;
-      const uint4 d = *reinterpret_cast<const uint4*>(dY + v * Cout + c8 * 8);
-      const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        *reinterpret_cast<uint16_t*>(A + y * WG_AP + (c8 * 8 + e) * 16 + x * 2) = h[e];
+    for (int blk = warp; blk < na; blk += NWARPS) {
+      const int y = blk & 15, c8 = blk >> 4;
+      const int64_t v = ((int64_t)(b * s.D + z) * s.H + y0 + y) * s.W + x0 + xr;
+      const uint32_t d = movm_trans(*reinterpret_cast<const uint32_t*>(dY + v * Cout + c8 * 8 + cp));
+      *reinterpret_cast<uint32_t*>(A + y * WG_AP + (c8 * 8 + xr) * 16 + cp * 2) = d;
     }
-    // XT[dxi][zp][yp][ci][x] = X[(x0 + x + dxi - 1, y0 + yp - 1, z + zp - 1)][16 g + ci];
-    // a warp's lanes take 8 x by 4 consecutive (dxi, zp, yp) blocks
+    // XT[dxi][zp][yp][ci][x] = X[(x0 + x + dxi - 1, y0 + yp - 1, z + zp - 1)][16 g + ci]:
+    // blocks of (8 x) x (8 ci), hh = which half of the 16 channels
 #pragma unroll 4
-    for (int i = tid; i < 2 * 164 * 8; i += WG_THREADS) {
-      const int x = i & 7, blk = ((i >> 5) % 41) * 4 + ((i >> 3) & 3), hh = (i >> 5) / 41;
-      if (blk >= 3 * 3 * 18) continue;
+    for (int blk2 = warp; blk2 < 2 * 3 * 3 * 18; blk2 += NWARPS) {
+      const int hh = blk2 & 1, blk = blk2 >> 1;
       const int yp = blk % 18, zp = (blk / 18) % 3, dxi = blk / 54;
-      int xx = x0 + x + dxi - 1, yy = y0 + yp - 1, zz = z + zp - 1;
+      int xx = x0 + xr + dxi - 1, yy = y0 + yp - 1, zz = z + zp - 1;
       xx = xx < 0 ? xx + s.W : (xx >= s.W ? xx - s.W : xx);
       yy = yy < 0 ? yy + s.H : (yy >= s.H ? yy - s.H : yy);
       zz = zz < 0 ? zz + s.D : (zz >= s.D ? zz - s.D : zz);
       const int64_t v = ((int64_t)(b * s.D + zz) * s.H + yy) * s.W + xx;
-      const uint4 d = *reinterpret_cast<const uint4*>(X + v * Cin + g * 16 + hh * 8);
-      const uint16_t* h = reinterpret_cast<const uint16_t*>(&d);
-      uint8_t* row = XT + blk * WG_XP + hh * 8 * 16 + x * 2;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) *reinterpret_cast<uint16_t*>(row + e * 16) = h[e];
+      const uint32_t d =
+          movm_trans(*reinterpret_cast<const uint32_t*>(X + v * Cin + g * 16 + hh * 8 + cp));
+      *reinterpret_cast<uint32_t*>(XT + blk * WG_XP + (hh * 8 + xr) * 16 + cp * 2) = d;
     }
     fence_proxy_async_smem();
   };
@@ -405,20 +418,24 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __rest
       tc_fence_after_sync();
       const uint8_t* A = wg_smem + buf * WG_BUF;
       const uint8_t* XT = A + WG_A;
-      for (int t = 0; t < 27; ++t) {
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;   // offsets + 1
+      // the operands' descriptors advance from the buffer's first ones; B rows
+      // (dy, ci): K halves WG_XP apart, 8-row groups 128 bytes apart
+      const uint64_t dA = umma_smem_desc(A, WG_AP, 128), dX = umma_smem_desc(XT, WG_XP, 128);
+      for (int dz = 0; dz < 3; ++dz)
+        for (int dx = 0; dx < 3; ++dx) {
+          const uint64_t dXt = umma_desc_advance(dX, ((dx * 3 + dz) * 18) * WG_XP);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          umma_bf16(tmem + (uint32_t)(t * 16), umma_smem_desc(A + j * 2 * WG_AP, WG_AP, 128),
-                    umma_smem_desc(XT + ((dx * 3 + dz) * 18 + 2 * j + dy) * WG_XP, WG_XP, 128),
-                    idesc, (it > 0 || j > 0) ? 1u : 0u);
-      }
+          for (int j = 0; j < 8; ++j)
+            umma_bf16(tmem + (uint32_t)((dz * 3 + dx) * 48), umma_desc_advance(dA, j * 2 * WG_AP),
+                      umma_desc_advance(dXt, 2 * j * WG_XP), idesc, (it > 0 || j > 0) ? 1u : 0u);
+        }
       umma_commit(&mbar[buf]);
     }
     const int q1 = q0 + gridDim.x;
     if (q1 < ntiles) {
       // the other buffer was read by the MMAs of tile it - 1
       if (it >= 1) ok = mbar_wait(&mbar[buf ^ 1], ((it - 1) >> 1) & 1, CONV_WAIT);
+      ok = __all_sync(0xffffffffu, ok);   // the staging's movmatrix needs whole warps
       if (ok) stage(q1, buf ^ 1);
     }
     ok = __syncthreads_and(ok);          // a timed-out wait ends the loop of the whole CTA
@@ -427,11 +444,13 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc(const bf16* __rest
   note_timeout(ok);
   tc_fence_after_sync();
   if (warp < 4) {                                            // TMEM lanes 0..127 = co
-    const int co = warp * 32 + (tid & 31);
+    const int co = warp * 32 + lane;
 #pragma unroll 1
     for (int t = 0; t < 27; ++t) {
+      const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
       float y[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 16), y);
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((dz * 3 + dx) * 48 + dy * 16),
+                y);
       if (co >= Cout) continue;
 #pragma unroll
       for (int e = 0; e < 16; ++e)
@@ -468,7 +487,8 @@ constexpr int WT_BP = 16 * 16 + 16;                       // 272 bytes per y row
 constexpr int WT_B = 8 * WT_BP;                           // 2176
 constexpr int WT_BUF = WT_XT + WT_B;                      // one stage's operands
 constexpr int WT_SMEM = 2 * WT_BUF;
-static_assert(WT_BUF % 16 == 0, "stage buffers on 16-byte boundaries");
+static_assert(WT_BUF % 16 == 0 && WT_XP % 16 == 0 && WT_BP % 16 == 0,
+              "stage buffers and operand offsets on 16-byte boundaries");
 static_assert(WT_SMEM > 114 * 1024 && WT_SMEM <= 227 * 1024, "one CTA per SM");
 __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc_t(const bf16* __restrict__ X,
                                                                 Vol s, int Cin,
@@ -558,15 +578,16 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_wgrad_tc_t(const bf16* __re
       const uint8_t* XT = wt_smem + buf * WT_BUF;
       const uint8_t* Bo = XT + WT_XT;
       const int dx = st % 3, lt = st / 3;
+      // the operands' descriptors advance from the buffer's first ones
+      const uint64_t dX = umma_smem_desc(XT, WT_XP, 128), dB = umma_smem_desc(Bo, WT_BP, 128);
       for (int dz = 0; dz < 3; ++dz)
         for (int dy = 0; dy < 3; ++dy) {
           const int t = dz * 9 + dy * 3 + dx;
+          const uint64_t dXt = umma_desc_advance(dX, (dz * 10 + dy) * WT_XP);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            umma_bf16(tmem + (uint32_t)(t * 16),
-                      umma_smem_desc(XT + (dz * 10 + 2 * j + dy) * WT_XP, WT_XP, 128),
-                      umma_smem_desc(Bo + j * 2 * WT_BP, WT_BP, 128), idesc,
-                      (lt > 0 || j > 0) ? 1u : 0u);
+            umma_bf16(tmem + (uint32_t)(t * 16), umma_desc_advance(dXt, 2 * j * WT_XP),
+                      umma_desc_advance(dB, j * 2 * WT_BP), idesc, (lt > 0 || j > 0) ? 1u : 0u);
         }
       umma_commit(&mbar[buf]);
     }
@@ -645,14 +666,19 @@ __global__ void __launch_bounds__(256) k_bias_grad_part(const bf16* __restrict__
   }
 }
 
-// Stage 2: db[c] = sum over the CTAs of part[b][c], in CTA order.
-__global__ void k_bias_grad_final(const double* __restrict__ part, int nblocks, int C,
-                                  float* __restrict__ db) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
+// Stage 2: db[c] = sum over the CTAs of part[b][c], one warp per channel: lane l
+// adds the CTAs l, l + 32, ... in order, then the lanes are combined by a
+// shuffle tree (a fixed order, so the result is deterministic).
+__global__ void __launch_bounds__(256) k_bias_grad_final(const double* __restrict__ part,
+                                                         int nblocks, int C,
+                                                         float* __restrict__ db) {
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (c >= C) return;                                       // whole warps leave together
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * C + c];
-  db[c] = (float)s;
+  for (int b = lane; b < nblocks; b += 32) s += part[(int64_t)b * C + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) db[c] = (float)s;
 }
 
 // ------------------------------------------------------------------ layer ops
@@ -930,15 +956,15 @@ __global__ void __launch_bounds__(128) k_conv_fwd_halo(const bf16* __restrict__ 
     }
   };
   // the G MMAs of tap t, B from buffer src; the first MMA of the call overwrites D
+  // (descriptors advanced from the tile's and the buffer's first ones)
   auto mma_tap = [&](int t, const uint8_t* src, bool first) {
     const int tap = (t / 9) * (HALO_TX * HALO_TY) + ((t / 3) % 3) * HALO_TX + t % 3;
+    const uint64_t dT = umma_smem_desc(tile, HALO_PLANE * 16, HALO_TX * 16);
+    const uint64_t dS = umma_smem_desc(src, N * 16, 128);
 #pragma unroll
     for (int c = 0; c < G; ++c)
-      umma_bf16(tmem,
-                umma_smem_desc(tile + (c * 2 * HALO_PLANE + tap) * 16, HALO_PLANE * 16,
-                               HALO_TX * 16),
-                umma_smem_desc(src + c * (N * 32), N * 16, 128), idesc,
-                (first && c == 0) ? 0u : 1u);
+      umma_bf16(tmem, umma_desc_advance(dT, (c * 2 * HALO_PLANE + tap) * 16),
+                umma_desc_advance(dS, c * (N * 32)), idesc, (first && c == 0) ? 0u : 1u);
   };
   bool ok = true;
   int last = 0;                                                // index of the last commit
@@ -1269,7 +1295,7 @@ claire_status claire_unet_bias_grad(const void* dy, long long V, int C, float* d
   const int64_t chunk = (V + nblocks - 1) / nblocks;
   const int nb = (int)((V + chunk - 1) / chunk);           // CTAs that own voxels
   k_bias_grad_part<<<nb, 256, 0, st>>>((const bf16*)dy, V, C, chunk, partial);
-  k_bias_grad_final<<<(C + 255) / 256, 256, 0, st>>>(partial, nb, C, db);
+  k_bias_grad_final<<<(C + 7) / 8, 256, 0, st>>>(partial, nb, C, db);
   return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
 }
 
