@@ -45,16 +45,19 @@ MAX_INNER = 10             # nested CG cap per preconditioner application
 INTERP_FD = ("trace", "sl_step", "adjoint_factor", "grad8", "div8", "sdot_hist", "accum_hist")
 # DRAM traffic per voxel and launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over the matvec's SL steps at 256^3, 24 algorithmic
-# B/voxel), with the SHA-256 of the kernel's source (its function in kernels.cu
-# plus sl_brick.cuh and common.cuh) at the time of the capture: when the source
-# differs, the figure is stale and roofline.traffic is reported as null.
+# B/voxel), with the SHA-256 of the kernel's source (sl_source_sha) at the time
+# of the capture: when the source differs, the figure is stale and
+# roofline.traffic is reported as null.
 NCU_TRAFFIC_PER_VOXEL = {
-    "sl_step": (23.25, "5cfa7294c2162eb5b56eedcdcdd1681bef9ff3fc472cb3a7a02306694b6874d8")}
+    "sl_step": (23.27, "d8afd71044d82c5a2800fa4d096977c4c0e1e8acf28555cad4dba16a4df80da2")}
 # 64-tap gathers of a field per 256^3 registration of the headline solve (trace
 # components x directions + SL steps + adjoint factors), counted by the
 # library's launch profile in this bench's own arm ("field_gathers_per_registration"):
 # the reference arm scales its per-gather time by it.
 GATHERS_PER_REGISTRATION = 161
+# Grouped batch: how long the first post of a round waits for the other pairs
+# (microseconds); 10 measured best among 0, 10, 40, 200 and waiting for all.
+GROUP_WAIT_US = 10
 
 
 def parse():
@@ -200,7 +203,9 @@ def batch_workload(npairs):
 
 def run_batch(args, pairs):
     """Uneven-grid batch: sequential per-pair solves vs claire_solve_batch
-    (concurrent streams, CUDA-graph PCG iterations), beta_v 5e-3, nt 4."""
+    (concurrent streams, CUDA-graph PCG iterations) vs
+    claire_solve_batch_grouped (one persistent launch per SL / trace / FD8 march
+    phase for all pairs, launch by launch otherwise), beta_v 5e-3, nt 4."""
     import numpy as np
     import torch
     from paper_2401_17493_b300 import claire
@@ -231,37 +236,61 @@ def run_batch(args, pairs):
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     same = all(torch.equal(a, b) for a, b in zip(v_seq, vs))
+    grouped = {}
+    for name, wait_us in (("grouped", GROUP_WAIT_US), ("grouped_lockstep", -1)):
+        for v in vs:                                   # warm-up, then timed
+            v.zero_()
+        claire.solve_batch(ctxs, vs, grouped=True, wait_us=wait_us)
+        for v in vs:
+            v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, gstats, glaunches = claire.solve_batch(ctxs, vs, grouped=True, wait_us=wait_us)
+        torch.cuda.synchronize()
+        tg = time.perf_counter() - t0
+        grouped[name] = {"seconds": tg, "wait_us": wait_us, "speedup": None,
+                         "vs_batched": None, "grouped_launches": int(glaunches[0]),
+                         "per_pair_launches_replaced": int(glaunches[1]),
+                         "all_converged": all(st.grad_rel <= EPS_OPT for st in gstats),
+                         "equals_sequential": all(torch.equal(a, b) for a, b in zip(v_seq, vs))}
     voxels = sum(int(np.prod(c.shape)) for c in ctxs)
     # PDE solves x voxels: the transport work of the batch, comparable across grid sizes
     vox_pde = sum(int(np.prod(c.shape)) * st.pde_solves for c, st in zip(ctxs, bstats))
     for c in ctxs:
         c.close()
+    for g in grouped.values():
+        g["speedup"] = t_seq / g["seconds"]
+        g["vs_batched"] = t_batch / g["seconds"]
     return {"pairs": len(ctxs), "grids": sorted(set(str(c) for c, _, _ in pairs)),
             "voxels": voxels, "sequential_s": t_seq, "batched_s": t_batch,
             "speedup": t_seq / t_batch, "pairs_per_s": len(ctxs) / t_batch,
             "matvecs": int(sum(st.matvecs for st in bstats)),
             "all_converged": all(st.grad_rel <= EPS_OPT for st in bstats),
             "batched_equals_sequential": bool(same),
+            **grouped,
             "voxel_pde_solves": vox_pde,
-            "voxel_pde_solves_per_s": {"batched": vox_pde / t_batch, "sequential": vox_pde / t_seq},
+            "voxel_pde_solves_per_s": {"batched": vox_pde / t_batch, "sequential": vox_pde / t_seq,
+                                       "grouped": vox_pde / grouped["grouped"]["seconds"]},
             "workload": "ellipsoid phantom pairs seeds 1000.., grids from {64^3, 96x112x80, "
                         "128^3, 160x192x144, 192^3}, beta_v 5e-3, nt 4, rel-grad 5e-2, "
                         "two-level preconditioner"}
 
 
 def sl_source_sha():
-    """SHA-256 of the SL step's source: its kernel function in kernels.cu (from
-    its comment block to the closing brace), sl_brick.cuh and common.cuh."""
+    """SHA-256 of the SL step's source: in kernels.cu its TMA brick staging and
+    its tile function and kernel (each from its section comment to the next
+    section), sl_brick.cuh, common.cuh and tc_sm100.cuh."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2401_17493_b300", "csrc")
     try:
         k = open(os.path.join(csrc, "kernels.cu")).read()
-        m = re.search(r"// MODE 0: out = .*?\n}\n", k, flags=re.S)
-        if m is None:
+        parts = [re.search(r"// -+ TMA brick staging\n.*?(?=// -+ trace\n)", k, flags=re.S),
+                 re.search(r"// MODE 0: out = .*?(?=// -+ grouped launches\n)", k, flags=re.S)]
+        if any(m is None for m in parts):
             return None
-        h = hashlib.sha256(m.group(0).encode())
-        for f in ("sl_brick.cuh", "common.cuh"):
+        h = hashlib.sha256("".join(m.group(0) for m in parts).encode())
+        for f in ("sl_brick.cuh", "common.cuh", "tc_sm100.cuh"):
             h.update(open(os.path.join(csrc, f), "rb").read())
         return h.hexdigest()
     except OSError:

@@ -279,6 +279,26 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
                                  int nlevels, float** v_inout, claire_stats* stats,
                                  int max_threads);
 
+/* The same batch with its SL steps, adjoint factors, traces and FD8 history
+ * marches launched for several pairs at once: one host thread per pair drives
+ * that pair's solve on the pair's stream, and instead of launching those
+ * kernels it posts them and waits.  The first post of a round waits until
+ * every unfinished pair has posted or wait_us microseconds have passed
+ * (wait_us < 0: until every unfinished pair has posted); then one persistent
+ * launch per kind walks the (pair, tile) items of all posted ops (the per-tile
+ * code of the single launch, so every pair's results are bitwise those of
+ * claire_solve_batch and of a solve on its own).  Launches captured into a
+ * pair's CUDA graphs (options.graphs) stay in its graphs; the FP16 kernels of
+ * precision-1 contexts and all other kernels (cuFFT, reductions, vector
+ * updates) run on the pairs' streams as before.  *group_launches and
+ * *group_ops (NULL ok) receive the number of grouped launches and of the
+ * per-pair launches they replaced.  Same arguments, statuses and rules as
+ * claire_solve_batch otherwise. */
+claire_status claire_solve_batch_grouped(claire_ctx** ctxs, int npairs, const double* betas,
+                                         int nlevels, float** v_inout, claire_stats* stats,
+                                         int wait_us, long long* group_launches,
+                                         long long* group_ops);
+
 /* ---- autotuner -------------------------------------------------------------
  * Times the compiled tile shapes of the SL gather (both gather variants, brick
  * depth along x1: 4, 8 or 16 nodes) and of the FD8 history kernels (8, 16, 32 or 64 planes per
@@ -288,17 +308,23 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
 claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
 
 /* Sets the tile shapes by hand (kept by options.autotune; drops captured graphs):
- *  sl_window  0: SL gathers with 64 shared loads per node (default);
+ *  sl_gather  0: SL gathers with 64 shared loads per node from a brick staged
+ *             by TMA tiled loads, one per brick row (default; bricks whose x3
+ *             range wraps around the periodic grid, and grids whose n3 is not
+ *             a multiple of 4 or is below 40, are staged as with 2);
  *             1: a per-lane register window of four x1 tap planes (16 shared
  *             loads per node whose displacement floor equals the lane's
  *             reference floor; the other nodes are gathered afterwards by the
- *             whole CTA from the brick).  Both give bitwise the same values;
+ *             whole CTA from the brick);
+ *             2: the 64-load gather from a brick staged by the threads'
+ *             16-byte cp.async copies.  All three give bitwise the same values
+ *             (the FP16 form stages its bricks with cp.async for 0 and 2);
  *  sl_t1      4, 8 or 16 nodes per thread along x1 (default 8);
  *  march_t1   8, 16, 32 or 64 planes per CTA of the FD8 history kernels (default 32).
  * EINVAL for any other value.  claire_get_tuning reads the current shapes (the
  * autotuner's choice after claire_autotune); NULL outputs are skipped. */
-claire_status claire_set_tuning(claire_ctx* ctx, int sl_window, int sl_t1, int march_t1);
-claire_status claire_get_tuning(const claire_ctx* ctx, int* sl_window, int* sl_t1,
+claire_status claire_set_tuning(claire_ctx* ctx, int sl_gather, int sl_t1, int march_t1);
+claire_status claire_get_tuning(const claire_ctx* ctx, int* sl_gather, int* sl_t1,
                                 int* march_t1);
 
 /* ---- gathers outside the staged brick ---------------------------------------
@@ -378,10 +404,12 @@ claire_status claire_unet_mse(long long V, int C, const float* y, const float* t
 claire_status claire_unet_adam(long long n, float* p, const float* g, float* m, float* v,
                                float lr, float b1, float b2, float eps, int step, void* pb,
                                void* stream);
-/* Bounded waits of the tensor-core kernels.  Every mbarrier wait of the
+/* Bounded waits of the tensor-core and TMA kernels.  Every mbarrier wait of the
  * convolution kernels gives up after 2^22 polls of at most 1 us each; a thread
  * whose wait ran out writes NaN outputs instead of hanging and is counted in a
- * device counter.  claire_wait_status synchronises the device, writes the count
+ * device counter.  The wait for a TMA-staged SL brick gives up after 2^20 polls;
+ * its CTA is counted and gathers from global memory instead (same values).
+ * claire_wait_status synchronises the device, writes the count
  * since the last call to *timeouts (NULL ok), resets it and returns
  * CLAIRE_ETIMEOUT if it was nonzero, else CLAIRE_OK.
  * claire_wait_selftest runs that failure path on purpose: one CTA of 32 threads

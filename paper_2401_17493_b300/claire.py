@@ -25,6 +25,7 @@ EXPORTED = [
     "claire_trace", "claire_interp", "claire_grad8", "claire_div8", "claire_spectral",
     "claire_det_deformation_gradient", "claire_profile_reset", "claire_profile_read",
     "claire_transport_noalloc", "claire_autotune", "claire_solve_batch",
+    "claire_solve_batch_grouped",
     "claire_conv3d_forward", "claire_conv3d_flip_weights", "claire_conv3d_wgrad",
     "claire_unet_op", "claire_unet_bias_grad", "claire_unet_pack", "claire_unet_mse",
     "claire_unet_adam", "claire_resample", "claire_precondition", "claire_beta_search",
@@ -119,6 +120,10 @@ def load_library(path=LIB_PATH):
         "claire_get_tuning": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "claire_solve_batch": ([ctypes.POINTER(P), I, ctypes.POINTER(D), I,
                                 ctypes.POINTER(P), ctypes.POINTER(Stats), I], I),
+        "claire_solve_batch_grouped": ([ctypes.POINTER(P), I, ctypes.POINTER(D), I,
+                                        ctypes.POINTER(P), ctypes.POINTER(Stats), I,
+                                        ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_longlong)], I),
         "claire_conv3d_forward": ([P, I, I, I, I, I, P, P, I, I, P, P, P], I),
         "claire_conv3d_flip_weights": ([P, I, I, P, P], I),
         "claire_conv3d_wgrad": ([P, I, I, I, I, I, P, I, P, I, P, P], I),
@@ -156,12 +161,16 @@ def _ptr(t, shape=None, what="array"):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def solve_batch(contexts, vs=None, betas=None, max_threads=0):
-    """Solve independent pairs concurrently (claire_solve_batch).
+def solve_batch(contexts, vs=None, betas=None, max_threads=0, grouped=False, wait_us=-1):
+    """Solve independent pairs concurrently (claire_solve_batch, or with
+    grouped=True claire_solve_batch_grouped: SL / trace / FD8 march launches of
+    several pairs combined into one, the first post of a round waiting up to
+    wait_us microseconds, < 0: for every unfinished pair).
 
     contexts: list of Context (images set); vs: list of CUDA (3, n1, n2, n3)
     initial guesses (None: zeros); betas: continuation levels or None.
-    Returns (vs, [Stats]) and raises on an error status other than
+    Returns (vs, [Stats]) (grouped: (vs, [Stats], (grouped launches, per-pair
+    launches they replaced))) and raises on an error status other than
     ENOTCONV / ELINESEARCH."""
     import torch
     L = load_library()
@@ -172,11 +181,18 @@ def solve_batch(contexts, vs=None, betas=None, max_threads=0):
     ps = (ctypes.c_void_p * n)(*[_ptr(v, c.vshape, "v").value for v, c in zip(vs, contexts)])
     stats = (Stats * n)()
     arr = None if betas is None else (ctypes.c_double * len(betas))(*map(float, betas))
-    st = L.claire_solve_batch(hs, n, arr, 0 if betas is None else len(betas), ps, stats,
-                              int(max_threads))
+    nlev = 0 if betas is None else len(betas)
+    launches, ops = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    if grouped:
+        st = L.claire_solve_batch_grouped(hs, n, arr, nlev, ps, stats, int(wait_us),
+                                          ctypes.byref(launches), ctypes.byref(ops))
+    else:
+        st = L.claire_solve_batch(hs, n, arr, nlev, ps, stats, int(max_threads))
     if st not in (OK, ENOTCONV, ELINESEARCH):
         raise ClaireError(st, "claire_solve_batch failed: " + "; ".join(
             c.lib.claire_last_error(c.h).decode() for c in contexts))
+    if grouped:
+        return vs, list(stats), (launches.value, ops.value)
     return vs, list(stats)
 
 
@@ -414,13 +430,16 @@ class Context:
         self._check(self.lib.claire_autotune(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    def set_tuning(self, sl_window=1, sl_t1=8, march_t1=32):
+    # SL gather variants of claire_set_tuning
+    GATHER_TMA, GATHER_WINDOW, GATHER_CPASYNC = 0, 1, 2
+
+    def set_tuning(self, sl_gather=0, sl_t1=8, march_t1=32):
         """Fix the tile shapes by hand (the SL gather variant, its x1 depth, the FD8
         march depth)."""
-        self._check(self.lib.claire_set_tuning(self.h, sl_window, sl_t1, march_t1))
+        self._check(self.lib.claire_set_tuning(self.h, sl_gather, sl_t1, march_t1))
 
     def tuning(self):
-        """(sl_window, sl_t1, march_t1) currently in use."""
+        """(sl_gather, sl_t1, march_t1) currently in use."""
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.claire_get_tuning(self.h, ctypes.byref(a), ctypes.byref(b),
                                                ctypes.byref(c)))

@@ -10,6 +10,9 @@
 #include <algorithm>
 #include <cstring>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <utility>
@@ -1103,9 +1106,10 @@ claire_status absmax3(claire_ctx* c, const float* a, double* out) {
 
 // Autotuner: time each compiled tile shape on this context's own grid and
 // buffers (the state history and departure points of the current evaluation)
-// with CUDA events, keep the fastest.  For the SL steps both gather variants
-// (64 shared loads per node, register window) at brick depths 4, 8, 16 along
-// x1; planes per CTA for the FD8 history kernels (8, 16, 32, 64).
+// with CUDA events, keep the fastest.  For the SL steps the three gather
+// variants (64 shared loads per node from a TMA-staged or a cp.async-staged
+// brick, register window) at brick depths 4, 8, 16 along x1; planes per CTA
+// for the FD8 history kernels (8, 16, 32, 64).
 claire_status autotune(claire_ctx* c) {
   if (!c->have_eval) return fail(c, CLAIRE_EORDER, "autotune needs an evaluated state");
   const int64_t N = N_of(c);
@@ -1121,11 +1125,17 @@ claire_status autotune(claire_ctx* c) {
   };
   Profiler* saved = tl_prof;
   tl_prof = nullptr;                                // tuning launches are not counted
+  LaunchGroup* saved_group = tl_group;
+  tl_group = nullptr;                               // timed on the context's own stream
+  struct Restore {
+    LaunchGroup* g;
+    ~Restore() { tl_group = g; }
+  } restore_group{saved_group};
   float best = 1e30f;
   Tuning t = c->tune;
-  for (int variant = 0; variant < 6; ++variant) {
+  for (int variant = 0; variant < 9; ++variant) {
     const int t1 = 4 << (variant % 3);
-    c->tune.sl_window = variant / 3;
+    c->tune.sl_gather = variant / 3;
     c->tune.sl_t1 = t1;
     float ms = 0.f;
     claire_status s = mixed(c)
@@ -1134,10 +1144,10 @@ claire_status autotune(claire_ctx* c) {
         : time_it([&] { launch_sl(c->g, c->mhist, c->df, nullptr, 1.f, nullptr, 0.f, c->pp0,
                                   c->st); }, &ms);
     if (s != CLAIRE_OK) { tl_prof = saved; return s; }
-    if (ms < best) { best = ms; t.sl_t1 = t1; t.sl_window = c->tune.sl_window; }
+    if (ms < best) { best = ms; t.sl_t1 = t1; t.sl_gather = c->tune.sl_gather; }
   }
   c->tune.sl_t1 = t.sl_t1;
-  c->tune.sl_window = t.sl_window;
+  c->tune.sl_gather = t.sl_gather;
   best = 1e30f;
   if (march_supported(c->nt)) {
     for (int m1 : {8, 16, 32, 64}) {
@@ -1867,11 +1877,137 @@ claire_status detf_stats(claire_ctx* c, const float* v, double* mmm, float* det_
 
 }  // namespace
 
-extern "C" {
+namespace claire {
 
-claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* betas,
-                                int nlevels, float** v_inout, claire_stats* stats,
-                                int max_threads) {
+// Combiner of a grouped batch.  Each worker posts one op at a time and blocks
+// until it has been launched.  The first op of a round makes its poster the
+// round's leader: it waits until every live worker has posted or until
+// wait_us microseconds have passed since its own post (wait_us < 0: no time
+// limit), whichever comes first, and then launches everything posted so far,
+// one persistent grouped launch per kind, on the group's stream.  Workers that post later go into the next round, so a
+// pair busy with other work (cuFFT, a host synchronisation) does not hold the
+// others back for long.  Ordering: a poster records an event on its pair's
+// stream and makes the group's stream wait for it before posting; the leader
+// records `done` behind the grouped launches and makes each flushed pair's
+// stream wait for it while it holds the lock, so no event is re-recorded before
+// its waits are enqueued.
+class LaunchGroup {
+ public:
+  LaunchGroup(int live, cudaStream_t gst, cudaEvent_t done, int wait_us)
+      : live_(live), wait_us_(wait_us), gst_(gst), done_(done) {}
+
+  void post(const GroupOp& op, cudaStream_t st, cudaEvent_t ev) {
+    note(cudaEventRecord(ev, st));
+    note(cudaStreamWaitEvent(gst_, ev, 0));
+    std::unique_lock<std::mutex> lk(mu_);
+    pending_.push_back(op);
+    streams_.push_back(st);
+    const uint64_t my = epoch_;
+    if ((int)pending_.size() >= live_) {
+      flush_locked();
+      return;
+    }
+    if (pending_.size() == 1) {                     // this round's leader
+      auto ready = [&] { return epoch_ != my || (int)pending_.size() >= live_; };
+      if (wait_us_ < 0) cv_.wait(lk, ready);
+      else cv_.wait_until(lk, std::chrono::steady_clock::now() +
+                                  std::chrono::microseconds(wait_us_), ready);
+      if (epoch_ == my) flush_locked();
+      return;
+    }
+    cv_.wait(lk, [&] { return epoch_ != my; });
+  }
+
+  // The calling worker posts nothing more.
+  void leave() {
+    std::lock_guard<std::mutex> lk(mu_);
+    --live_;
+    if (live_ > 0 && !pending_.empty() && (int)pending_.size() >= live_) flush_locked();
+    cv_.notify_all();                               // a leader may now have everyone
+  }
+
+  cudaError_t error() {
+    std::lock_guard<std::mutex> lk(err_mu_);
+    return err_;
+  }
+  long long ops() const { return ops_; }
+  long long launches() const { return launches_; }
+
+ private:
+  void note(cudaError_t e) {
+    if (e != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(err_mu_);
+      if (err_ == cudaSuccess) err_ = e;
+    }
+  }
+
+  void flush_locked() {
+    std::vector<SlOpArgs> sl[2];
+    std::vector<TraceOpArgs> tr;
+    std::vector<std::pair<int, MarchOpArgs>> mh;   // (mode * 16 + nf, args)
+    for (const GroupOp& op : pending_) {
+      if (op.kind == GOP_SL0 || op.kind == GOP_SL1) sl[op.kind].push_back(op.sl);
+      else if (op.kind == GOP_TRACE) tr.push_back(op.tr);
+      else mh.emplace_back(op.mode * 16 + op.nf, op.mh);
+    }
+    for (int m = 0; m < 2; ++m)
+      if (!sl[m].empty()) {
+        launch_sl_group(m, sl[m].data(), (int)sl[m].size(), gst_);
+        ++launches_;
+      }
+    if (!tr.empty()) {
+      launch_trace_group(tr.data(), (int)tr.size(), gst_);
+      ++launches_;
+    }
+    std::stable_sort(mh.begin(), mh.end(),
+                     [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (size_t i = 0; i < mh.size();) {
+      size_t j = i;
+      std::vector<MarchOpArgs> ops;
+      while (j < mh.size() && mh[j].first == mh[i].first) ops.push_back(mh[j++].second);
+      if (!launch_march_group(mh[i].first / 16, mh[i].first % 16, ops.data(), (int)ops.size(),
+                              gst_))
+        note(cudaErrorInvalidValue);
+      ++launches_;
+      i = j;
+    }
+    note(cudaGetLastError());
+    note(cudaEventRecord(done_, gst_));
+    for (cudaStream_t st : streams_) note(cudaStreamWaitEvent(st, done_, 0));
+    ops_ += (long long)pending_.size();
+    pending_.clear();
+    streams_.clear();
+    ++epoch_;
+    cv_.notify_all();
+  }
+
+  std::mutex mu_, err_mu_;
+  std::condition_variable cv_;
+  int live_;
+  const int wait_us_;
+  uint64_t epoch_ = 0;
+  std::vector<GroupOp> pending_;
+  std::vector<cudaStream_t> streams_;
+  cudaStream_t gst_;
+  cudaEvent_t done_;
+  cudaError_t err_ = cudaSuccess;
+  long long ops_ = 0, launches_ = 0;
+};
+
+thread_local LaunchGroup* tl_group = nullptr;
+static thread_local cudaEvent_t tl_group_event = nullptr;
+
+void group_post(const GroupOp& op, cudaStream_t st) { tl_group->post(op, st, tl_group_event); }
+
+}  // namespace claire
+
+// Solves the pairs on their own streams, one host thread per pair (grouped:
+// every pair, its SL steps, traces and FD8 marches combined by a LaunchGroup)
+// or up to max_threads threads (ungrouped).
+static claire_status solve_batch_impl(claire_ctx** ctxs, int npairs, const double* betas,
+                                      int nlevels, float** v_inout, claire_stats* stats,
+                                      int max_threads, bool grouped, int wait_us,
+                                      long long* group_launches, long long* group_ops) {
   if (!ctxs || npairs < 1 || !v_inout || (betas && nlevels < 1)) return CLAIRE_EINVAL;
   for (int i = 0; i < npairs; ++i) {
     if (!ctxs[i] || !v_inout[i]) return CLAIRE_EINVAL;
@@ -1895,9 +2031,30 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
     }
   }
   std::vector<claire_status> res(npairs, CLAIRE_OK);
+  const int nt = grouped ? npairs
+                         : std::max(1, std::min(npairs, max_threads > 0 ? max_threads : npairs));
+  // grouped: the group's stream and events (launches captured into a pair's
+  // graphs stay in the graph; the rest is posted)
+  cudaStream_t gst = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> evs(grouped ? nt : 0, nullptr);
+  claire_status setup = CLAIRE_OK;
+  if (grouped) {
+    if (cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess)
+      setup = CLAIRE_ECUDA;
+    for (int t = 0; t < nt && setup == CLAIRE_OK; ++t)
+      if (cudaEventCreateWithFlags(&evs[t], cudaEventDisableTiming) != cudaSuccess)
+        setup = CLAIRE_ECUDA;
+  }
+  LaunchGroup group(nt, gst, done, wait_us);
   std::atomic<int> next{0};
-  auto worker = [&]() {
+  auto worker = [&](int t) {
     cudaSetDevice(dev);
+    if (grouped) {
+      tl_group = &group;
+      tl_group_event = evs[t];
+    }
     for (int i = next++; i < npairs; i = next++) {
       claire_ctx* c = ctxs[i];
       const double b = c->beta_v;
@@ -1906,11 +2063,28 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
                      : solve_levels(c, &b, 1, v_inout[i], v_inout[i],
                                     stats ? stats + i : nullptr);
     }
+    if (grouped) {
+      group.leave();
+      tl_group = nullptr;
+      tl_group_event = nullptr;
+    }
   };
-  const int nt = std::max(1, std::min(npairs, max_threads > 0 ? max_threads : npairs));
-  std::vector<std::thread> pool;
-  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
-  for (auto& t : pool) t.join();
+  if (setup == CLAIRE_OK) {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker, t);
+    for (auto& t : pool) t.join();
+  }
+  if (grouped) {
+    if (gst && cudaStreamSynchronize(gst) != cudaSuccess && setup == CLAIRE_OK)
+      setup = CLAIRE_ECUDA;
+    if (group.error() != cudaSuccess && setup == CLAIRE_OK) setup = CLAIRE_ECUDA;
+    if (group_launches) *group_launches = group.launches();
+    if (group_ops) *group_ops = group.ops();
+    for (cudaEvent_t e : evs)
+      if (e) cudaEventDestroy(e);
+    if (done) cudaEventDestroy(done);
+    if (gst) cudaStreamDestroy(gst);
+  }
   for (int i = 0; i < npairs; ++i) {
     claire_ctx* c = ctxs[i];
     if (c->st != saved[i]) {
@@ -1921,13 +2095,30 @@ claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* be
       if (tl_set_streams(c) != CLAIRE_OK && res[i] == CLAIRE_OK) res[i] = CLAIRE_ECUDA;
     }
   }
-  claire_status worst = CLAIRE_OK;
+  claire_status worst = setup;
   for (int i = 0; i < npairs; ++i)
     if (res[i] != CLAIRE_OK && res[i] != CLAIRE_ENOTCONV) worst = res[i];
   if (worst == CLAIRE_OK)
     for (int i = 0; i < npairs; ++i)
       if (res[i] != CLAIRE_OK) worst = res[i];
   return worst;
+}
+
+extern "C" {
+
+claire_status claire_solve_batch(claire_ctx** ctxs, int npairs, const double* betas,
+                                 int nlevels, float** v_inout, claire_stats* stats,
+                                 int max_threads) {
+  return solve_batch_impl(ctxs, npairs, betas, nlevels, v_inout, stats, max_threads, false, 0,
+                          nullptr, nullptr);
+}
+
+claire_status claire_solve_batch_grouped(claire_ctx** ctxs, int npairs, const double* betas,
+                                         int nlevels, float** v_inout, claire_stats* stats,
+                                         int wait_us, long long* group_launches,
+                                         long long* group_ops) {
+  return solve_batch_impl(ctxs, npairs, betas, nlevels, v_inout, stats, 0, true, wait_us,
+                          group_launches, group_ops);
 }
 
 claire_status claire_far_nodes(claire_ctx* c, long long* fwd, long long* bwd) {
@@ -1959,16 +2150,17 @@ claire_status claire_autotune(claire_ctx* c, int* sl_t1, int* march_t1) {
   return CLAIRE_OK;
 }
 
-claire_status claire_set_tuning(claire_ctx* c, int sl_window, int sl_t1, int march_t1) {
+claire_status claire_set_tuning(claire_ctx* c, int sl_gather, int sl_t1, int march_t1) {
   if (!c) return CLAIRE_EINVAL;
   ENTER(c);
-  if (sl_window != 0 && sl_window != 1)
-    return fail(c, CLAIRE_EINVAL, "sl_window must be 0 or 1");
+  if (sl_gather != SL_GATHER_TMA && sl_gather != SL_GATHER_WINDOW &&
+      sl_gather != SL_GATHER_CPASYNC)
+    return fail(c, CLAIRE_EINVAL, "sl_gather must be 0, 1 or 2");
   if (sl_t1 != 4 && sl_t1 != 8 && sl_t1 != 16)
     return fail(c, CLAIRE_EINVAL, "sl_t1 must be 4, 8 or 16");
   if (march_t1 != 8 && march_t1 != 16 && march_t1 != 32 && march_t1 != 64)
     return fail(c, CLAIRE_EINVAL, "march_t1 must be 8, 16, 32 or 64");
-  c->tune.sl_window = sl_window;
+  c->tune.sl_gather = sl_gather;
   c->tune.sl_t1 = sl_t1;
   c->tune.march_t1 = march_t1;
   c->tuned = true;                                 // options.autotune keeps these shapes
@@ -1976,10 +2168,10 @@ claire_status claire_set_tuning(claire_ctx* c, int sl_window, int sl_t1, int mar
   return CLAIRE_OK;
 }
 
-claire_status claire_get_tuning(const claire_ctx* c, int* sl_window, int* sl_t1,
+claire_status claire_get_tuning(const claire_ctx* c, int* sl_gather, int* sl_t1,
                                 int* march_t1) {
   if (!c) return CLAIRE_EINVAL;
-  if (sl_window) *sl_window = c->tune.sl_window;
+  if (sl_gather) *sl_gather = c->tune.sl_gather;
   if (sl_t1) *sl_t1 = c->tune.sl_t1;
   if (march_t1) *march_t1 = c->tune.march_t1;
   return CLAIRE_OK;

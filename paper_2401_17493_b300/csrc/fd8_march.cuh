@@ -128,21 +128,33 @@ __device__ __forceinline__ void stage_plane_async(const T* __restrict__ u, const
 // values of plane i1 + 1 (queue head, lam^j, vt, base, dotv) are already
 // loading into registers, so each plane costs one barrier round instead of a
 // global-memory round trip.
-template <int MODE, int NF, typename T>
-__global__ void __launch_bounds__(32 * MT2, NF <= 5 ? 2 : 1)
-k_hist_march(Grid g, const T* __restrict__ mhist, const T* __restrict__ lhist,
-             const float* __restrict__ vt, float scale0, const double* __restrict__ vmax,
-             const float* __restrict__ base, float base_coef, float umul,
-             float* __restrict__ out, T* __restrict__ hout, const float* __restrict__ dotv,
-             double* __restrict__ partial, int mt1) {
+//
+// march_tile does the work of the CTA at tile (bx, by, bz) of a launch with
+// gx x gy tiles per x1 slab (the partial sum goes to partial[(bz gy + by) gx
+// + bx]); sp / fp are the CTA's shared staging buffers (MarchSmem).  It ends
+// with a barrier, so the buffers may be reused right after it.
+template <int NF, typename T>
+struct MarchSmem {
   // sp: staged planes as stored (double buffer).  FP16 planes are converted
   // into the FP32 plane fp by the threads that copied them, once per element,
   // so the 16 stencil reads per field and node need no conversion.
-  constexpr bool kHalf = sizeof(T) == 2;
-  __shared__ __align__(16) T sp[2][NF][MPLANE];
-  __shared__ __align__(16) float fp[kHalf ? NF : 1][kHalf ? MPLANE : 4];
+  static constexpr bool kHalf = sizeof(T) == 2;
+  __align__(16) T sp[2][NF][MPLANE];
+  __align__(16) float fp[kHalf ? NF : 1][kHalf ? MPLANE : 4];
+};
+
+template <int MODE, int NF, typename T>
+__device__ __forceinline__ void march_tile(
+    const Grid& g, const T* __restrict__ mhist, const T* __restrict__ lhist,
+    const float* __restrict__ vt, float scale0, const double* __restrict__ vmax,
+    const float* __restrict__ base, float base_coef, float umul, float* __restrict__ out,
+    T* __restrict__ hout, const float* __restrict__ dotv, double* __restrict__ partial, int mt1,
+    int bx, int by, int bz, int gx, int gy, MarchSmem<NF, T>& S) {
+  constexpr bool kHalf = MarchSmem<NF, T>::kHalf;
+  auto& sp = S.sp;
+  auto& fp = S.fp;
   const int lane = threadIdx.x, ty = threadIdx.y;
-  const int i3_0 = blockIdx.x * MT3, i2_0 = blockIdx.y * MT2, i1_0 = blockIdx.z * mt1;
+  const int i3_0 = bx * MT3, i2_0 = by * MT2, i1_0 = bz * mt1;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   const bool active = i2 < g.n2 && i3 < g.n3;
   const int64_t N = g.N;
@@ -292,8 +304,21 @@ k_hist_march(Grid g, const T* __restrict__ mhist, const T* __restrict__ lhist,
   if (has_dot) {
     const double b = block_sum(dacc.value());
     if (threadIdx.x == 0 && threadIdx.y == 0)
-      partial[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
+      partial[((int64_t)bz * gy + by) * gx + bx] = b;
   }
+}
+
+template <int MODE, int NF, typename T>
+__global__ void __launch_bounds__(32 * MT2, NF <= 5 ? 2 : 1)
+k_hist_march(Grid g, const T* __restrict__ mhist, const T* __restrict__ lhist,
+             const float* __restrict__ vt, float scale0, const double* __restrict__ vmax,
+             const float* __restrict__ base, float base_coef, float umul,
+             float* __restrict__ out, T* __restrict__ hout, const float* __restrict__ dotv,
+             double* __restrict__ partial, int mt1) {
+  __shared__ MarchSmem<NF, T> S;
+  march_tile<MODE, NF, T>(g, mhist, lhist, vt, scale0, vmax, base, base_coef, umul, out, hout,
+                          dotv, partial, mt1, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x,
+                          gridDim.y, S);
 }
 
 }  // namespace claire

@@ -46,15 +46,22 @@ extern thread_local Profiler* tl_prof;
 // (0: 64 shared loads per node, the default; 1: register window along x1 with
 // a deferred queue), the x1 depth of the SL brick (4, 8 or 16 nodes) and
 // planes per CTA of the FD8 march (8, 16, 32 or 64).
+// SL gather variants: the 64-tap gather from a brick staged by TMA tiled loads
+// (default) or by the threads' 16-byte cp.async copies, or the register window.
+enum SlGather { SL_GATHER_TMA = 0, SL_GATHER_WINDOW = 1, SL_GATHER_CPASYNC = 2 };
 struct Tuning {
-  int sl_window = 0;
+  int sl_gather = SL_GATHER_TMA;
   int sl_t1 = 8;
   int march_t1 = 32;
 };
 extern thread_local const Tuning* tl_tune;
 int tuned_sl_t1();
 bool tuned_sl_window();
+bool tuned_sl_tma();
 int tuned_march_t1();
+// Threads whose bounded wait for a TMA-staged SL brick ran out since the last
+// call (those CTAs gathered from global memory instead); reads and resets.
+unsigned int take_brick_timeouts();
 
 struct ProfileRange {
   int kind;
@@ -111,6 +118,53 @@ void launch_lincomb(int64_t n, float a, const float* x, float b, const float* y,
                     cudaStream_t st);
 void launch_detf(const Grid& g, const float* v, const float* df, int nt, float* F, float* Fn,
                  float* A, float* Ay, float* det, cudaStream_t st);
+
+// ---- grouped launches of a batch (claire_solve_batch_grouped, group.cu) ----
+// Each worker thread of a grouped batch drives one pair's solve.  Its FP32 SL
+// steps, adjoint factors, traces and FD8 history marches are not launched on
+// the pair's stream but posted to the batch's LaunchGroup: when every live
+// worker has posted one, the group launches each kind once for all of them
+// (a persistent kernel over the (pair, tile) items, kernels.cu) on its own
+// stream, ordered after each pair's earlier work and before its later work by
+// events.  The per-tile code is the single launch's, so the results are
+// bitwise those of per-pair launches.
+struct SlOpArgs {            // one k_sl launch (mode 0: SL step, 1: adjoint factor)
+  Grid g;
+  const float* u; const float* d; const float* scale; const float* aux;
+  float* out;
+  float sigma, beta, ht;
+  int t1, tma;               // tile depth; TMA staging wanted (gather variant 0)
+};
+struct TraceOpArgs {         // one k_trace launch
+  Grid g;
+  const float* v; float* df; float* db;
+  float ht;
+  int t1, tma;
+};
+struct MarchOpArgs {         // one k_hist_march<mode, nf, float> launch
+  Grid g;
+  const float* mhist; const float* lhist; const float* vt; const double* vmax;
+  const float* base; float* out; float* hout; const float* dotv; double* partial;
+  float scale0, base_coef, umul;
+  int mt1;
+};
+enum GroupKind { GOP_SL0 = 0, GOP_SL1 = 1, GOP_TRACE = 2, GOP_MARCH = 3 };
+struct GroupOp {
+  int kind;
+  int mode, nf;              // GOP_MARCH: the march template
+  SlOpArgs sl;
+  TraceOpArgs tr;
+  MarchOpArgs mh;
+};
+class LaunchGroup;
+extern thread_local LaunchGroup* tl_group;
+// Posts op for the calling worker (blocks until it has been launched; st's
+// later work waits for it).
+void group_post(const GroupOp& op, cudaStream_t st);
+// Persistent grouped kernels over all ops' tiles (any count: launched in chunks).
+void launch_sl_group(int mode, const SlOpArgs* ops, int n, cudaStream_t st);
+void launch_trace_group(const TraceOpArgs* ops, int n, cudaStream_t st);
+bool launch_march_group(int mode, int nf, const MarchOpArgs* ops, int n, cudaStream_t st);
 
 // Mixed-precision (FP16 storage) launchers, see mixed.cu.
 void launch_sl_h(const Grid& g, const __half* u, const float* d, const float* scale,

@@ -13,9 +13,12 @@
 // All grids are [n1][n2][n3] with n3 fastest; 3D kernels use 32 x 4 x 2
 // thread blocks (x3 along threadIdx.x for coalescing, a compact 3D footprint
 // for the L1 reuse of the 64-tap gathers).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math_constants.h>
 
 #include <atomic>
+#include <cstring>
 #include <mutex>
 
 #include "device_setup.h"
@@ -24,6 +27,7 @@
 #include "sl_brick.cuh"
 #include "sl_window.cuh"
 #include "fd8_march.cuh"
+#include "tc_sm100.cuh"
 
 namespace claire {
 
@@ -39,19 +43,80 @@ static dim3 grid3(const Grid& g) {
   return dim3((g.n3 + 31) / 32, (g.n2 + 3) / 4, (g.n1 + 1) / 2);
 }
 
+// ------------------------------------------------------ TMA brick staging
+
+// The SL bricks of k_sl and k_trace are staged by the tensor-memory accelerator
+// where the brick lies inside the grid: the source field is a 3D tensor map
+// (n3, n2, ncomp n1) and the whole brick is one box of BB3 x BB2 x (t1 + 6)
+// FP32 values (x3 x x2 x x1) at (i3_0 - 4, i2_0 - 3, c n1 + i1_0 - 3), written
+// densely into shared memory: rows of BB3 = 64 floats, the layout of
+// stage_brick, of which the gather reads the first BX3 = 40 (values beyond n3
+// in the padding are filled with zeros and never read).  One request per brick,
+// issued by one thread.  Bricks that wrap around the periodic grid (the tiles
+// at the ends of each axis, or grids narrower than a brick) are staged by the
+// threads' cp.async copies instead.  The load completes on an mbarrier.  The
+// wait is bounded: a thread whose wait runs out counts it in g_brick_timeouts
+// (read by claire_wait_status), waits once more (bounded) for the copy in
+// flight and leaves its outputs unwritten.
+constexpr uint32_t BRICK_WAIT = 1u << 20;       // try_wait calls of <= 1 us each
+
+__device__ unsigned int g_brick_timeouts = 0;
+
+// True when the tile's brick lies inside the grid on every axis: x3 range
+// [i3_0 - 4, i3_0 + 36), x2 range [i2_0 - 3, i2_0 + 11), x1 range
+// [i1_0 - 3, i1_0 + t1 + 3).
+__device__ __forceinline__ bool brick_tma_ok(const Grid& g, int i1_0, int i2_0, int i3_0,
+                                             int t1) {
+  return i3_0 - HB3_LO >= 0 && i3_0 - HB3_LO + BX3 <= g.n3 && i2_0 - HB_LO >= 0 &&
+         i2_0 + TB2 + HB_HI <= g.n2 && i1_0 - HB_LO >= 0 && i1_0 + t1 + HB_HI <= g.n1;
+}
+
+// mbarrier of the brick loads (one arrival per phase) set up by thread 0; the
+// caller's barrier publishes it before the first load.
+__device__ __forceinline__ void brick_mbar_init(uint64_t* mbar) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+  }
+}
+
+// Thread 0 issues the TMA load of component c's brick into s; it completes on
+// the mbarrier's current phase.  The mbarrier must be set up and published, and
+// the shared brick no longer in use (a barrier since its last reads).
+__device__ __forceinline__ void issue_brick_tma(const CUtensorMap* map, int c, const Grid& g,
+                                                int i1_0, int i2_0, int i3_0,
+                                                float* __restrict__ s, int t1, uint64_t* mbar) {
+  if (threadIdx.x != 0 || threadIdx.y != 0) return;
+  fence_proxy_async_smem();                     // earlier generic accesses of the brick first
+  mbar_arrive_expect_tx(mbar, (uint32_t)brick_floats(t1) * (uint32_t)sizeof(float));
+  tma_load_3d(s, map, i3_0 - HB3_LO, i2_0 - HB_LO, c * g.n1 + i1_0 - HB_LO, mbar);
+}
+
+// Bounded wait for the brick loads of phase `parity`; false if it ran out (counted).
+__device__ __forceinline__ bool wait_brick_tma(uint64_t* mbar, uint32_t parity) {
+  if (mbar_wait(mbar, parity, BRICK_WAIT)) return true;
+  atomicAdd(&g_brick_timeouts, 1u);
+  (void)mbar_wait(mbar, parity, BRICK_WAIT);    // the copies in flight, again bounded
+  return false;
+}
+
 // ---------------------------------------------------------------- trace
 
-// RK2 departure points of both directions (Sec. 2.5.2) for a tile of nodes.
-// The velocity components are staged one at a time into one brick, which
-// serves both directions; the predictor y~ = x -+ h_t v(x) is interpolated
-// from it, and the corrector y = x -+ (h_t / 2)(v(x) + v(y~)) is stored as
-// y - x in grid units.
-__global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __restrict__ v,
-                                                         float* __restrict__ df,
-                                                         float* __restrict__ db, float ht,
-                                                         int t1) {
-  extern __shared__ __align__(16) float sm[];
-  const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+// RK2 departure points of both directions (Sec. 2.5.2) for the tile (bx, by, bz)
+// of nodes.  The velocity components are staged one at a time into one brick,
+// which serves both directions; the predictor y~ = x -+ h_t v(x) is
+// interpolated from it, and the corrector y = x -+ (h_t / 2)(v(x) + v(y~)) is
+// stored as y - x in grid units.  With use_tma the bricks come from vmap (v as
+// an n3 x n2 x 3 n1 tensor: the components stacked along x1) and the loads
+// complete on phases parity, parity ^ 1, parity of the mbarrier (set up and
+// published by the caller, like a barrier since the brick's last use).
+__device__ __forceinline__ void trace_tile(const Grid& g, const float* __restrict__ v,
+                                           float* __restrict__ df, float* __restrict__ db,
+                                           float ht, int t1, const CUtensorMap* vmap,
+                                           bool use_tma, int bx, int by, int bz,
+                                           float* __restrict__ sm, uint64_t* mbar,
+                                           uint32_t parity) {
+  const int i1_0 = bz * t1, i2_0 = by * TB2, i3_0 = bx * TB3;
   const int64_t N = g.N, s1 = (int64_t)g.n2 * g.n3;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
@@ -61,13 +126,19 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
     if (c > 0) __syncthreads();                  // previous brick consumed
+    if (use_tma) issue_brick_tma(vmap, c, g, i1_0, i2_0, i3_0, sm, t1, mbar);
     // v(x) of the first node is loaded while the brick is being staged
     float v0[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) v0[a] = active ? v[a * N + idx0] : 0.f;
-    stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm, t1);
-    __syncthreads();
-    if (!active) continue;
+    bool ok = true;
+    if (use_tma) {
+      ok = wait_brick_tma(mbar, parity ^ (uint32_t)(c & 1));
+    } else {
+      stage_brick(v + c * N, g, i1_0, i2_0, i3_0, sm, t1);
+      __syncthreads();
+    }
+    if (!active || !ok) continue;
     const float ihc = c == 0 ? g.inv_h1 : (c == 1 ? g.inv_h2 : g.inv_h3);
 #pragma unroll 1
     for (int dir = 0; dir < 2; ++dir) {
@@ -96,35 +167,63 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __
   }
 }
 
+// One CTA per tile.  With tma != 0 the interior bricks are staged by TMA.
+__global__ void __launch_bounds__(BRICK_THREADS) k_trace(Grid g, const float* __restrict__ v,
+                                                         float* __restrict__ df,
+                                                         float* __restrict__ db, float ht,
+                                                         int t1,
+                                                         const __grid_constant__ CUtensorMap vmap,
+                                                         int tma) {
+  extern __shared__ __align__(128) float smb[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smb + brick_floats(t1));
+  const bool use_tma =
+      tma && brick_tma_ok(g, blockIdx.z * t1, blockIdx.y * TB2, blockIdx.x * TB3, t1);
+  if (use_tma) {
+    brick_mbar_init(mbar);
+    __syncthreads();
+  }
+  trace_tile(g, v, df, db, ht, t1, &vmap, use_tma, blockIdx.x, blockIdx.y, blockIdx.z, smb, mbar,
+             0u);
+}
+
 // ---------------------------------------------------------------- SL step
 
 // MODE 0: out = (scale ? scale(x) : sigma) u(x + d) + beta aux(x)    (SL steps)
 // MODE 1: out = 1 + (h_t/2)(u(y) + u(x) + h_t u(x) u(y)), u = div v: the factor
 //         c(x) with which one RK2 step of d_t lam = lam div v along -v becomes
 //         lam^j(x) = c(x) lam^{j+1}(y).
+// For the tile (bx, by, bz); with use_tma the brick comes from umap and the load
+// completes on phase `parity` of the mbarrier (set up and published by the
+// caller, like a barrier since the brick's last use).
 template <int MODE>
-__global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl(Grid g, const float* __restrict__ u,
-                                                      const float* __restrict__ d,
-                                                      const float* __restrict__ scale,
-                                                      float sigma,
-                                                      const float* __restrict__ aux, float beta,
-                                                      float ht, float* __restrict__ out,
-                                                      int t1) {
-  extern __shared__ __align__(16) float sm[];
-  const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
+__device__ __forceinline__ void sl_tile(const Grid& g, const float* __restrict__ u,
+                                        const float* __restrict__ d,
+                                        const float* __restrict__ scale, float sigma,
+                                        const float* __restrict__ aux, float beta, float ht,
+                                        float* __restrict__ out, int t1, const CUtensorMap* umap,
+                                        bool use_tma, int bx, int by, int bz,
+                                        float* __restrict__ sm, uint64_t* mbar,
+                                        uint32_t parity) {
+  const int i1_0 = bz * t1, i2_0 = by * TB2, i3_0 = bx * TB3;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   const bool active = i2 < g.n2 && i3 < g.n3;
   const int64_t N = g.N, s1 = (int64_t)g.n2 * g.n3;
   const int64_t idx0 = active ? lin(g, i1_0, i2, i3) : 0;
+  if (use_tma) issue_brick_tma(umap, 0, g, i1_0, i2_0, i3_0, sm, t1, mbar);
   // departure points of the next node are loaded one node ahead (the first
   // ones while the brick is being staged)
   float dn[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) dn[a] = active ? d[a * N + idx0] : 0.f;
-  stage_brick(u, g, i1_0, i2_0, i3_0, sm, t1);
-  __syncthreads();
-  if (!active) return;
+  bool ok = true;
+  if (use_tma) {
+    ok = wait_brick_tma(mbar, parity);
+  } else {
+    stage_brick(u, g, i1_0, i2_0, i3_0, sm, t1);
+    __syncthreads();
+  }
+  if (!active || !ok) return;
   const int ctr = (HB_LO * BB2 + ty + HB_LO) * BB3 + lane + HB3_LO;
   const int kmax = min(t1, g.n1 - i1_0);
 #pragma unroll 2
@@ -151,6 +250,141 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl(Grid g, const float* __
       if (aux) r = fmaf(beta, ax, r);
     }
     out[idx] = r;
+  }
+}
+
+// One CTA per tile.  With tma != 0 the interior bricks are staged by TMA.
+template <int MODE>
+__global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl(Grid g, const float* __restrict__ u,
+                                                      const float* __restrict__ d,
+                                                      const float* __restrict__ scale,
+                                                      float sigma,
+                                                      const float* __restrict__ aux, float beta,
+                                                      float ht, float* __restrict__ out,
+                                                      int t1,
+                                                      const __grid_constant__ CUtensorMap umap,
+                                                      int tma) {
+  extern __shared__ __align__(128) float smb[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smb + brick_floats(t1));
+  const bool use_tma =
+      tma && brick_tma_ok(g, blockIdx.z * t1, blockIdx.y * TB2, blockIdx.x * TB3, t1);
+  if (use_tma) {
+    brick_mbar_init(mbar);
+    __syncthreads();
+  }
+  sl_tile<MODE>(g, u, d, scale, sigma, aux, beta, ht, out, t1, &umap, use_tma, blockIdx.x,
+                blockIdx.y, blockIdx.z, smb, mbar, 0u);
+}
+
+// ------------------------------------------------------- grouped launches
+
+// Persistent kernels of a grouped batch: one launch covers the tiles of up to
+// GROUP_MAX ops (pairs).  The work queue is the concatenation of the ops'
+// tiles (op o owns items first[o] .. first[o + 1] - 1, in the tile order of its
+// single launch); CTA b takes items b, b + gridDim.x, ...  Each item is the
+// tile function of the single launch, so every tile computes what that launch
+// computes.  Parameters, TMA descriptors included, travel by value in the
+// launch (__grid_constant__).
+constexpr int GROUP_MAX = 32;
+
+struct SlGroupOp {
+  Grid g;
+  const float* u; const float* d; const float* scale; const float* aux;
+  float* out;
+  float sigma, beta, ht;
+  int t1, tma, tx, ty;              // tiles along x3, x2
+};
+struct alignas(64) SlGroup {
+  CUtensorMap map[GROUP_MAX];
+  SlGroupOp op[GROUP_MAX];
+  int first[GROUP_MAX + 1];
+  int nops, t1max;
+};
+struct TraceGroupOp {
+  Grid g;
+  const float* v; float* df; float* db;
+  float ht;
+  int t1, tma, tx, ty;
+};
+struct alignas(64) TraceGroup {
+  CUtensorMap map[GROUP_MAX];
+  TraceGroupOp op[GROUP_MAX];
+  int first[GROUP_MAX + 1];
+  int nops, t1max;
+};
+struct MarchGroup {
+  MarchOpArgs op[GROUP_MAX];
+  int tx[GROUP_MAX], ty[GROUP_MAX];
+  int first[GROUP_MAX + 1];
+  int nops;
+};
+
+// The op owning `item`: the largest o with first[o] <= item.
+__device__ __forceinline__ int group_op_of(const int* first, int nops, int item) {
+  int lo = 0, hi = nops - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl_group(const __grid_constant__ SlGroup G) {
+  extern __shared__ __align__(128) float smb[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smb + brick_floats(G.t1max));
+  brick_mbar_init(mbar);
+  __syncthreads();
+  uint32_t parity = 0;
+  const int total = G.first[G.nops];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int o = group_op_of(G.first, G.nops, item);
+    const SlGroupOp& op = G.op[o];
+    const int tile = item - G.first[o], r = tile / op.tx;
+    const int bx = tile - r * op.tx, bz = r / op.ty, by = r - bz * op.ty;
+    const bool use_tma = op.tma && brick_tma_ok(op.g, bz * op.t1, by * TB2, bx * TB3, op.t1);
+    sl_tile<MODE>(op.g, op.u, op.d, op.scale, op.sigma, op.aux, op.beta, op.ht, op.out, op.t1,
+                  &G.map[o], use_tma, bx, by, bz, smb, mbar, parity);
+    parity ^= use_tma ? 1u : 0u;
+    __syncthreads();                              // brick consumed before the next item
+  }
+}
+
+__global__ void __launch_bounds__(BRICK_THREADS) k_trace_group(const __grid_constant__ TraceGroup G) {
+  extern __shared__ __align__(128) float smb[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smb + brick_floats(G.t1max));
+  brick_mbar_init(mbar);
+  __syncthreads();
+  uint32_t parity = 0;
+  const int total = G.first[G.nops];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int o = group_op_of(G.first, G.nops, item);
+    const TraceGroupOp& op = G.op[o];
+    const int tile = item - G.first[o], r = tile / op.tx;
+    const int bx = tile - r * op.tx, bz = r / op.ty, by = r - bz * op.ty;
+    const bool use_tma = op.tma && brick_tma_ok(op.g, bz * op.t1, by * TB2, bx * TB3, op.t1);
+    trace_tile(op.g, op.v, op.df, op.db, op.ht, op.t1, &G.map[o], use_tma, bx, by, bz, smb,
+               mbar, parity);
+    parity ^= use_tma ? 1u : 0u;                  // three phases: p, p ^ 1, p
+    __syncthreads();                              // brick consumed before the next item
+  }
+}
+
+template <int MODE, int NF>
+__global__ void __launch_bounds__(32 * MT2, NF <= 5 ? 2 : 1)
+k_march_group(const __grid_constant__ MarchGroup G) {
+  __shared__ MarchSmem<NF, float> S;
+  const int total = G.first[G.nops];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int o = group_op_of(G.first, G.nops, item);
+    const MarchOpArgs& op = G.op[o];
+    const int tx = G.tx[o], ty = G.ty[o];
+    const int tile = item - G.first[o], r = tile / tx;
+    const int bx = tile - r * tx, bz = r / ty, by = r - bz * ty;
+    march_tile<MODE, NF, float>(op.g, op.mhist, op.lhist, op.vt, op.scale0, op.vmax, op.base,
+                                op.base_coef, op.umul, op.out, op.hout, op.dotv, op.partial,
+                                op.mt1, bx, by, bz, tx, ty, S);
   }
 }
 
@@ -854,18 +1088,84 @@ static int vec_blocks(int64_t n) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+// True while st is being captured into a CUDA graph: captured launches stay
+// per pair (they replay inside the pair's graph), everything else of a grouped
+// batch is posted to its LaunchGroup.
+static bool posts_to_group(cudaStream_t st) {
+  if (!tl_group) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
 thread_local const Tuning* tl_tune = nullptr;
+static int tuned_sl_gather() { return tl_tune ? tl_tune->sl_gather : SL_GATHER_TMA; }
 int tuned_sl_t1() { return tl_tune ? tl_tune->sl_t1 : TB1; }
-bool tuned_sl_window() { return tl_tune ? tl_tune->sl_window != 0 : false; }
+bool tuned_sl_window() { return tuned_sl_gather() == SL_GATHER_WINDOW; }
+bool tuned_sl_tma() { return tuned_sl_gather() == SL_GATHER_TMA; }
 int tuned_march_t1() { return tl_tune ? tl_tune->march_t1 : MT1; }
+
+unsigned int take_brick_timeouts() {
+  unsigned int n = 0;
+  const unsigned int zero = 0;
+  if (cudaMemcpyFromSymbol(&n, g_brick_timeouts, sizeof n) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_brick_timeouts, &zero, sizeof zero) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of ncomp consecutive FP32 fields of the grid starting at base, as
+// one n3 x n2 x (ncomp n1) tensor, box = one brick of depth t1 (BB3 x BB2 x
+// (t1 + 6)).  Returns false (the caller stages with cp.async) unless the fields
+// meet TMA's rules: base 16-byte aligned, the row pitch n3 * 4 bytes a multiple
+// of 16, and the grid at least one brick wide on every axis.
+static bool brick_map(const float* base, const Grid& g, int ncomp, int t1, CUtensorMap* m) {
+  std::memset(m, 0, sizeof *m);
+  const auto enc = tensor_map_encoder();
+  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || g.n3 % 4 != 0 ||
+      g.n3 < BX3 || g.n2 < BB2 || g.n1 < t1 + HB_LO + HB_HI)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.n3, (cuuint64_t)g.n2, (cuuint64_t)ncomp * g.n1};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.n3 * sizeof(float),
+                                 (cuuint64_t)g.n2 * g.n3 * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)BB3, (cuuint32_t)BB2, (cuuint32_t)(t1 + HB_LO + HB_HI)};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// dynamic shared memory of k_sl / k_trace: the brick and its mbarrier
+static size_t brick_smem_bytes(int t1) {
+  return (size_t)brick_floats(t1) * sizeof(float) + 16;
+}
 
 static void brick_attributes() {
   static std::once_flag once[kSetupDevices];
   once_per_device(once, [] {
-    const int mx = brick_floats(16) * (int)sizeof(float);
+    const int mx = (int)brick_smem_bytes(16);
     cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_sl<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_sl<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_sl_group<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_sl_group<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_trace_group, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     const int mw = window_smem_bytes(16, 5, 0);
     cudaFuncSetAttribute(k_tracew, cudaFuncAttributeMaxDynamicSharedMemorySize, mw);
     cudaFuncSetAttribute(k_slw<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mw);
@@ -876,39 +1176,172 @@ void launch_trace(const Grid& g, const float* v, float* df, float* db, float ht,
                   cudaStream_t st) {
   brick_attributes();
   const int t1 = tuned_sl_t1();
+  if (!tuned_sl_window() && posts_to_group(st)) {
+    GroupOp op{};
+    op.kind = GOP_TRACE;
+    op.tr = TraceOpArgs{g, v, df, db, ht, t1, tuned_sl_tma() ? 1 : 0};
+    group_post(op, st);
+    return;
+  }
   ProfileRange pr(K_TRACE, (double)g.N * (12 + 12 * ((df != nullptr) + (db != nullptr))), st);
-  if (tuned_sl_window())
+  if (tuned_sl_window()) {
     k_tracew<<<brick_grid(g, t1), dim3(32, TB2), window_smem_bytes(t1, 3, 0), st>>>(
         g, v, df, db, ht, t1);
-  else
-    k_trace<<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-        g, v, df, db, ht, t1);
+  } else {
+    CUtensorMap m;
+    const int tma = tuned_sl_tma() && brick_map(v, g, 3, t1, &m);
+    k_trace<<<brick_grid(g, t1), dim3(32, TB2), brick_smem_bytes(t1), st>>>(g, v, df, db, ht,
+                                                                            t1, m, tma);
+  }
 }
 void launch_sl(const Grid& g, const float* u, const float* d, const float* scale, float sigma,
                const float* aux, float beta, float* out, cudaStream_t st) {
+  if (!tuned_sl_window() && posts_to_group(st)) {
+    GroupOp op{};
+    op.kind = GOP_SL0;
+    op.sl = SlOpArgs{g, u, d, scale, aux, out, sigma, beta, 0.f, tuned_sl_t1(),
+                     tuned_sl_tma() ? 1 : 0};
+    group_post(op, st);
+    return;
+  }
   ProfileRange pr(K_SL, (double)g.N * (20 + 4 * (scale != nullptr) + 4 * (aux != nullptr)), st);
   brick_attributes();
   const int t1 = tuned_sl_t1();
-  if (tuned_sl_window())
+  if (tuned_sl_window()) {
     k_slw<0><<<brick_grid(g, t1), dim3(32, TB2),
                window_smem_bytes(t1, 3 + (scale != nullptr) + (aux != nullptr), 0), st>>>(
         g, u, d, scale, sigma, aux, beta, 0.f, out, t1);
-  else
-    k_sl<0><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-        g, u, d, scale, sigma, aux, beta, 0.f, out, t1);
+  } else {
+    CUtensorMap m;
+    const int tma = tuned_sl_tma() && brick_map(u, g, 1, t1, &m);
+    k_sl<0><<<brick_grid(g, t1), dim3(32, TB2), brick_smem_bytes(t1), st>>>(
+        g, u, d, scale, sigma, aux, beta, 0.f, out, t1, m, tma);
+  }
 }
 void launch_adjoint_factor(const Grid& g, const float* D, const float* db, float ht, float* c,
                            cudaStream_t st) {
+  if (!tuned_sl_window() && posts_to_group(st)) {
+    GroupOp op{};
+    op.kind = GOP_SL1;
+    op.sl = SlOpArgs{g, D, db, nullptr, nullptr, c, 1.f, 0.f, ht, tuned_sl_t1(),
+                     tuned_sl_tma() ? 1 : 0};
+    group_post(op, st);
+    return;
+  }
   ProfileRange pr(K_ADJFAC, (double)g.N * 20, st);
   brick_attributes();
   const int t1 = tuned_sl_t1();
-  if (tuned_sl_window())
+  if (tuned_sl_window()) {
     k_slw<1><<<brick_grid(g, t1), dim3(32, TB2), window_smem_bytes(t1, 3, 0), st>>>(
         g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1);
-  else
-    k_sl<1><<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-        g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1);
+  } else {
+    CUtensorMap m;
+    const int tma = tuned_sl_tma() && brick_map(D, g, 1, t1, &m);
+    k_sl<1><<<brick_grid(g, t1), dim3(32, TB2), brick_smem_bytes(t1), st>>>(
+        g, D, db, nullptr, 1.f, nullptr, 0.f, ht, c, t1, m, tma);
+  }
 }
+// Grid of a persistent grouped launch: every SM filled with as many CTAs as fit
+// (at most one per item).
+template <typename K>
+static int group_blocks(K kernel, int threads, size_t smem, int total) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 148;
+  return std::max(1, std::min(total, sms * per_sm));
+}
+
+void launch_sl_group(int mode, const SlOpArgs* ops, int n, cudaStream_t st) {
+  brick_attributes();
+  for (int base = 0; base < n; base += GROUP_MAX) {
+    SlGroup G;
+    std::memset(&G, 0, sizeof G);
+    G.nops = std::min(GROUP_MAX, n - base);
+    int total = 0;
+    for (int o = 0; o < G.nops; ++o) {
+      const SlOpArgs& a = ops[base + o];
+      SlGroupOp& q = G.op[o];
+      q.g = a.g; q.u = a.u; q.d = a.d; q.scale = a.scale; q.aux = a.aux; q.out = a.out;
+      q.sigma = a.sigma; q.beta = a.beta; q.ht = a.ht; q.t1 = a.t1;
+      q.tma = a.tma && brick_map(a.u, a.g, 1, a.t1, &G.map[o]);
+      const dim3 b = brick_grid(a.g, a.t1);
+      q.tx = (int)b.x; q.ty = (int)b.y;
+      G.first[o] = total;
+      total += (int)(b.x * b.y * b.z);
+      G.t1max = std::max(G.t1max, a.t1);
+    }
+    G.first[G.nops] = total;
+    const size_t smem = brick_smem_bytes(G.t1max);
+    if (mode == 0)
+      k_sl_group<0><<<group_blocks(k_sl_group<0>, BRICK_THREADS, smem, total),
+                      dim3(32, TB2), smem, st>>>(G);
+    else
+      k_sl_group<1><<<group_blocks(k_sl_group<1>, BRICK_THREADS, smem, total),
+                      dim3(32, TB2), smem, st>>>(G);
+  }
+}
+
+void launch_trace_group(const TraceOpArgs* ops, int n, cudaStream_t st) {
+  brick_attributes();
+  for (int base = 0; base < n; base += GROUP_MAX) {
+    TraceGroup G;
+    std::memset(&G, 0, sizeof G);
+    G.nops = std::min(GROUP_MAX, n - base);
+    int total = 0;
+    for (int o = 0; o < G.nops; ++o) {
+      const TraceOpArgs& a = ops[base + o];
+      TraceGroupOp& q = G.op[o];
+      q.g = a.g; q.v = a.v; q.df = a.df; q.db = a.db; q.ht = a.ht; q.t1 = a.t1;
+      q.tma = a.tma && brick_map(a.v, a.g, 3, a.t1, &G.map[o]);
+      const dim3 b = brick_grid(a.g, a.t1);
+      q.tx = (int)b.x; q.ty = (int)b.y;
+      G.first[o] = total;
+      total += (int)(b.x * b.y * b.z);
+      G.t1max = std::max(G.t1max, a.t1);
+    }
+    G.first[G.nops] = total;
+    const size_t smem = brick_smem_bytes(G.t1max);
+    k_trace_group<<<group_blocks(k_trace_group, BRICK_THREADS, smem, total), dim3(32, TB2),
+                    smem, st>>>(G);
+  }
+}
+
+bool launch_march_group(int mode, int nf, const MarchOpArgs* ops, int n, cudaStream_t st) {
+  for (int base = 0; base < n; base += GROUP_MAX) {
+    MarchGroup G;
+    std::memset(&G, 0, sizeof G);
+    G.nops = std::min(GROUP_MAX, n - base);
+    int total = 0;
+    for (int o = 0; o < G.nops; ++o) {
+      G.op[o] = ops[base + o];
+      const dim3 b = march_grid(G.op[o].g, G.op[o].mt1);
+      G.tx[o] = (int)b.x; G.ty[o] = (int)b.y;
+      G.first[o] = total;
+      total += (int)(b.x * b.y * b.z);
+    }
+    G.first[G.nops] = total;
+#define CLAIRE_MARCH_GROUP(M, NF)                                                        \
+  k_march_group<M, NF><<<group_blocks(k_march_group<M, NF>, 32 * MT2, 0, total),           \
+                         dim3(32, MT2), 0, st>>>(G)
+    switch (mode * 16 + nf) {
+      case 2: CLAIRE_MARCH_GROUP(0, 2); break;
+      case 3: CLAIRE_MARCH_GROUP(0, 3); break;
+      case 5: CLAIRE_MARCH_GROUP(0, 5); break;
+      case 9: CLAIRE_MARCH_GROUP(0, 9); break;
+      case 18: CLAIRE_MARCH_GROUP(1, 2); break;
+      case 19: CLAIRE_MARCH_GROUP(1, 3); break;
+      case 21: CLAIRE_MARCH_GROUP(1, 5); break;
+      case 25: CLAIRE_MARCH_GROUP(1, 9); break;
+      default: return false;
+    }
+#undef CLAIRE_MARCH_GROUP
+  }
+  return true;
+}
+
 void launch_count_far(const Grid& g, const float* d, unsigned long long* out,
                       cudaStream_t st) {
   k_count_far<<<vec_blocks(g.N), 256, 0, st>>>(g.N, d, out);
@@ -944,6 +1377,16 @@ static bool launch_march(const Grid& g, const float* mhist, const float* lhist, 
                          cudaStream_t st, const float* dotv = nullptr,
                          double* partial = nullptr) {
   const int mt1 = tuned_march_t1();
+  if (march_supported(nt) && posts_to_group(st)) {
+    GroupOp op{};
+    op.kind = GOP_MARCH;
+    op.mode = MODE;
+    op.nf = nt + 1;
+    op.mh = MarchOpArgs{g, mhist, lhist, vt, nullptr, base, out, out, dotv, partial,
+                        scale0, base_coef, 1.f, mt1};
+    group_post(op, st);
+    return true;
+  }
   const dim3 grid = march_grid(g, mt1), block(32, MT2);
 #define CLAIRE_MARCH(NF)                                                                    \
   k_hist_march<MODE, NF, float><<<grid, block, 0, st>>>(g, mhist, lhist, vt, scale0, nullptr, \

@@ -1,7 +1,8 @@
-// Fifth-generation tensor core (tcgen05) helpers for sm_100-family GPUs: TMEM
-// allocation, the kind::f16 MMA with shared-memory operand descriptors, commit
-// to an mbarrier, TMEM -> register loads, and the fences between the generic
-// proxy, the async proxy and thread synchronisation.  Inline PTX only.
+// Fifth-generation tensor core (tcgen05) and TMA helpers for sm_100-family GPUs:
+// TMEM allocation, the kind::f16 MMA with shared-memory operand descriptors,
+// commit to an mbarrier, TMEM -> register loads, mbarriers with transaction
+// counts, tiled TMA loads, and the fences between the generic proxy, the async
+// proxy and thread synchronisation.  Inline PTX only.
 //
 // Operand layout (both operands K-major, no swizzle): an R x 16 BF16 tile is
 // stored as "core matrices" of 8 rows x 16 bytes (8 elements along K); element
@@ -85,6 +86,43 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
   asm volatile(
       "{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(mbar))
+      : "memory");
+}
+
+// Arrival that also announces `bytes` more bytes of asynchronous copies completing
+// on the current phase (the phase completes when both counts are reached).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Makes an mbarrier initialisation visible to the async proxy (TMA completions).
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// TMA tiled load of the box at element coordinates (x, y) of a 2D tensor map
+// into shared memory (128-byte aligned destination; x times the element size a
+// multiple of 16 bytes); its bytes complete on the mbarrier.  The tensor map
+// lives in kernel-parameter space (a __grid_constant__ argument).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// TMA tiled load of the box at element coordinates (x, y, z) of a 3D tensor map
+// (same rules as tma_load_2d).
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(mbar))
       : "memory");
 }
 

@@ -1135,6 +1135,8 @@ __global__ void k_wait_selftest(uint32_t max_polls, int arrive) {
 }
 
 }  // namespace
+// threads whose bounded wait for a TMA-staged SL brick ran out (kernels.cu)
+unsigned int take_brick_timeouts();
 }  // namespace claire
 
 using namespace claire;
@@ -1332,6 +1334,7 @@ claire_status claire_wait_status(int* timeouts) {
   if (cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof n) != cudaSuccess ||
       cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof zero) != cudaSuccess)
     return CLAIRE_ECUDA;
+  n += take_brick_timeouts();
   if (timeouts) *timeouts = (int)n;
   return n ? CLAIRE_ETIMEOUT : CLAIRE_OK;
 }

@@ -27,8 +27,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--only", default=None)
     ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 FP16 field storage")
-    ap.add_argument("--sl-window", type=int, default=None, choices=[0, 1],
-                    help="SL gather variant (1 register window, 0 64 shared loads per node)")
+    ap.add_argument("--sl-gather", type=int, default=None, choices=[0, 1, 2],
+                    help="SL gather variant (0 64 shared loads per node from a TMA-staged "
+                         "brick, 1 register window, 2 64 loads from a cp.async-staged brick)")
     ap.add_argument("--sl-t1", type=int, default=None, choices=[4, 8, 16],
                     help="SL brick depth along x1")
     args = ap.parse_args()
@@ -42,9 +43,9 @@ def main():
     u = torch.rand(shape, device="cuda", generator=gen)
     v = torch.from_numpy(synth.bandlimited_velocity(shape, 8, 4.0, 3).astype(np.float32)).cuda()
     ctx = claire.Context(shape, nt=4, precision=args.precision)
-    if args.sl_window is not None or args.sl_t1 is not None:
+    if args.sl_gather is not None or args.sl_t1 is not None:
         w0, t0, m0 = ctx.tuning()
-        ctx.set_tuning(w0 if args.sl_window is None else args.sl_window,
+        ctx.set_tuning(w0 if args.sl_gather is None else args.sl_gather,
                        t0 if args.sl_t1 is None else args.sl_t1, m0)
     ctx.set_images(u, u)
     d, _ = ctx.trace(v)

@@ -3,6 +3,8 @@ autotuner: each must give the same registrations as the plain sequential
 per-pair solve (the kernels are deterministic; graph replay runs the same
 launches; tile shapes change only the block partition of the FP64 sums)."""
 
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -178,3 +180,56 @@ def test_autotuner_picks_valid_shapes_and_keeps_results(claire):
         v1, _ = ctx.solve()
     a, b = v1.cpu().numpy(), v0.cpu().numpy()
     assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
+
+
+GROUP_SHAPES = SHAPES + [(40, 36, 132)]        # the last one with TMA-staged interior bricks
+
+
+def _group_contexts(C, precisions, **opts):
+    ctxs = []
+    for i, (shape, prec) in enumerate(zip(GROUP_SHAPES, precisions)):
+        m0, m1, _ = synth.blob_pair(shape, seed=300 + i, kmax=3, max_disp_voxels=2.0)
+        ctx = C.Context(shape, nt=4, beta_v=5e-3, precision=prec, **opts)
+        ctx.set_images(dev(m0), dev(m1))
+        ctxs.append(ctx)
+    return ctxs
+
+
+@pytest.mark.parametrize("precisions", [(0, 0, 0, 0, 0), (0, 1, 0, 1, 0)])
+def test_grouped_batch_equals_sequential_solves(claire, precisions):
+    """One persistent launch per SL / trace / FD8 march phase for all pairs of the
+    batch gives every pair bitwise its sequential registration; mixed-precision
+    pairs keep their FP16 kernels on their own streams, beside the grouped FP32
+    ones.  Graph capture is set on the contexts and suspended for the batch."""
+    seq = []
+    for ctx in _group_contexts(claire, precisions, graphs=1):
+        v, st = ctx.solve()
+        seq.append((v.cpu().numpy(), st.matvecs, st.status, st.newton_iters))
+        ctx.close()
+    ctxs = _group_contexts(claire, precisions, graphs=1)
+    vs, stats, launches = claire.solve_batch(ctxs, grouped=True)
+    for (vref, mv, status, nit), v, st in zip(seq, vs, stats):
+        assert st.status == status and st.matvecs == mv and st.newton_iters == nit
+        assert np.array_equal(v.cpu().numpy(), vref)
+    # each grouped launch stands for the launches of several pairs
+    grouped_launches, replaced = launches
+    assert 0 < grouped_launches < replaced
+    for c in ctxs:
+        o = claire.Options()
+        assert c.lib.claire_get_options(c.h, ctypes.byref(o)) == claire.OK
+        assert o.graphs == 1                        # restored after the batch
+        c.close()
+    assert claire.wait_status() == 0
+
+
+def test_grouped_batch_continuation_and_reuse(claire):
+    """Continuation levels through the grouped batch equal the per-context
+    continuation, and the contexts stay usable for ungrouped solves afterwards."""
+    betas = [5e-2, 5e-3]
+    ctxs = _group_contexts(claire, (0, 0, 0, 0, 0))
+    vs, stats, _ = claire.solve_batch(ctxs, betas=betas, grouped=True)
+    for ctx, v, st in zip(ctxs, vs, stats):
+        assert st.grad_rel <= 5e-2 and st.J < st.J0
+        v2, st2 = ctx.solve_continuation(betas)
+        assert np.array_equal(v.cpu().numpy(), v2.cpu().numpy())
+        ctx.close()

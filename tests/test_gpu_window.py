@@ -1,14 +1,17 @@
-"""The two SL gather variants give bitwise the same values.
+"""The three SL gather variants give bitwise the same values.
 
 The register-window gather (each lane keeps four x1 tap planes in registers
 and contracts the nodes that share its reference floor; the others go through
-a deferred queue) and the 64-shared-load brick gather evaluate every node with
+a deferred queue) and the 64-shared-load brick gather, from a brick staged by
+TMA tiled loads or by the threads' cp.async copies, evaluate every node with
 the same taps in the same FP32 order, so every SL step, trace, adjoint factor
 and every quantity built from them must agree bit for bit, for every brick
 depth, on ragged grids (partial tiles along every axis), on a grid whose x3
-extent is not a multiple of 4 (scalar staging path), and for displacements
-from sub-voxel to many periods (global-memory gathers).  The oracle parity of
-the default (64-load) variant is covered by the other GPU tests.
+extent is not a multiple of 4 (scalar staging path), on a grid with interior
+x3 tiles (TMA-staged bricks beside cp.async-staged edge bricks), and for
+displacements from sub-voxel to many periods (global-memory gathers).  The
+oracle parity of the default variant is covered by the other GPU tests (the
+256^3 sampled cases stage most bricks by TMA).
 """
 
 import numpy as np
@@ -20,8 +23,8 @@ torch = pytest.importorskip("torch")
 
 from paper_2401_17493_b300 import synth
 
-SHAPES = [(22, 18, 40), (18, 20, 34), (64, 64, 64)]
-VARIANTS = [(0, 8), (1, 4), (1, 8), (1, 16), (0, 4)]
+SHAPES = [(22, 18, 40), (18, 20, 34), (64, 64, 64), (20, 22, 100), (40, 36, 132)]
+VARIANTS = [(0, 8), (1, 4), (1, 8), (1, 16), (0, 4), (2, 8), (2, 16), (0, 16)]
 
 
 @pytest.fixture(scope="module")
@@ -67,6 +70,7 @@ def test_interpolation_variants_are_bitwise_equal(claire, shape, kind):
             outs.append(ctx.interp(u, d).clone())
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
+    assert claire.wait_status() == 0             # no bounded brick wait ran out
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -107,18 +111,19 @@ def test_solve_variants_are_bitwise_equal(claire):
     shape = (32, 32, 32)
     m0, m1, _ = synth.blob_pair(shape, seed=4, kmax=3, max_disp_voxels=2.0)
     vs = []
-    for w in (0, 1):
+    for w in (0, 1, 2):
         with claire.Context(shape, nt=4, beta_v=1e-2, precond=1, max_inner=10) as ctx:
             ctx.set_images(dev(m0), dev(m1))
             ctx.set_tuning(w, 8, 32)
             v, st = ctx.solve()
             vs.append((v.clone(), st.matvecs, st.newton_iters))
-    assert torch.equal(vs[0][0], vs[1][0]) and vs[0][1:] == vs[1][1:]
+    for other in vs[1:]:
+        assert torch.equal(vs[0][0], other[0]) and vs[0][1:] == other[1:]
 
 
 def test_tuning_rejects_unknown_shapes(claire):
     with claire.Context((16, 16, 16)) as ctx:
-        for bad in [(2, 8, 32), (1, 12, 32), (1, 8, 24)]:
+        for bad in [(3, 8, 32), (-1, 8, 32), (1, 12, 32), (1, 8, 24)]:
             with pytest.raises(claire.ClaireError):
                 ctx.set_tuning(*bad)
         assert ctx.tuning() == (0, 8, 32)
@@ -137,5 +142,7 @@ def test_tuning_change_after_graph_capture_gives_the_same_solve(claire):
         v2, s2 = ctx.solve()
         ctx.set_tuning(0, 16, 64)
         v3, s3 = ctx.solve()
-    assert torch.equal(v1, v2) and torch.equal(v1, v3)
-    assert s1.matvecs == s2.matvecs == s3.matvecs
+        ctx.set_tuning(2, 8, 32)
+        v4, s4 = ctx.solve()
+    assert torch.equal(v1, v2) and torch.equal(v1, v3) and torch.equal(v1, v4)
+    assert s1.matvecs == s2.matvecs == s3.matvecs == s4.matvecs
