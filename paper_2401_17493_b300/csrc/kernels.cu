@@ -3,7 +3,7 @@
 //  k_trace            RK2 departure points, both directions      (Sec. 2.5.2)
 //  k_sl               one SL step: out = s(x) gather(u, x + d) + beta aux(x)
 //  k_adjoint_factor   c(x) of the RK2 adjoint step with f = lam div v
-//  k_grad8 / k_div8   FD8 gradient / divergence                   (Sec. 2.5.3)
+//  k_grad8 / k_div8_march  FD8 gradient / divergence              (Sec. 2.5.3)
 //  k_sdot_hist        s^j = grad8(m^j) . v~ for the whole state history
 //  k_accum_hist       out = base_coef * base + sum_j w_j lam^j grad8(m^j)
 //  k_spectral         diagonal Fourier multipliers between cuFFT R2C / C2R
@@ -546,36 +546,6 @@ __global__ void __launch_bounds__(256) k_grad8(Grid g, const float* __restrict__
   gu[2 * g.N + idx] = gr[2];
 }
 
-__device__ __forceinline__ float d8_axis(const float* __restrict__ u, const Grid& g, int i1,
-                                         int i2, int i3, int axis) {
-  float m[4], p[4];
-  if (axis == 0) {
-    const int64_t s1 = (int64_t)g.n2 * g.n3;
-    const float* base = u + (int64_t)i2 * g.n3 + i3;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      m[k] = __ldg(base + wrap_near(i1 - 1 - k, g.n1) * s1);
-      p[k] = __ldg(base + wrap_near(i1 + 1 + k, g.n1) * s1);
-    }
-    return fd8(m[3], m[2], m[1], m[0], p[0], p[1], p[2], p[3], g.inv_h1);
-  } else if (axis == 1) {
-    const float* base = u + (int64_t)i1 * g.n2 * g.n3 + i3;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      m[k] = __ldg(base + (int64_t)wrap_near(i2 - 1 - k, g.n2) * g.n3);
-      p[k] = __ldg(base + (int64_t)wrap_near(i2 + 1 + k, g.n2) * g.n3);
-    }
-    return fd8(m[3], m[2], m[1], m[0], p[0], p[1], p[2], p[3], g.inv_h2);
-  }
-  const float* base = u + ((int64_t)i1 * g.n2 + i2) * g.n3;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    m[k] = __ldg(base + wrap_near(i3 - 1 - k, g.n3));
-    p[k] = __ldg(base + wrap_near(i3 + 1 + k, g.n3));
-  }
-  return fd8(m[3], m[2], m[1], m[0], p[0], p[1], p[2], p[3], g.inv_h3);
-}
-
 // FD8 derivative along `axis` of the product lam * u at node (i1, i2, i3).
 __device__ __forceinline__ float d8_axis_prod(const float* __restrict__ lam,
                                               const float* __restrict__ u, const Grid& g, int i1,
@@ -611,11 +581,63 @@ __global__ void __launch_bounds__(256) k_div8_prod(Grid g, const float* __restri
              d8_axis_prod(lam, w + 2 * g.N, g, i1, i2, i3, 2);
 }
 
-__global__ void __launch_bounds__(256) k_div8(Grid g, const float* __restrict__ w,
-                                              float* __restrict__ out) {
-  CLAIRE_KERNEL_INDEX
-  out[idx] = d8_axis(w, g, i1, i2, i3, 0) + d8_axis(w + g.N, g, i1, i2, i3, 1) +
-             d8_axis(w + 2 * g.N, g, i1, i2, i3, 2);
+
+// div8(w) marching along x1 (the layout of the FD8 history kernels): a CTA owns
+// an MT2 x MT3 (x2 x x3) tile and mt1 planes.  w1 goes through a 9-deep
+// register queue (the x1 derivative: each value read once), the planes of w2
+// and w3 with their 4-node halo are copied with cp.async into shared memory one
+// plane ahead (the x2 and x3 derivatives).  Per node: fd8() along each axis,
+// summed x1 + x2 + x3, with the x1 neighbours taken from registers instead of
+// eight plane reads per node.
+__global__ void __launch_bounds__(32 * MT2) k_div8_march(Grid g, const float* __restrict__ w,
+                                                         float* __restrict__ out, int mt1) {
+  __shared__ __align__(16) float sp[2][2][MPLANE];           // [buffer][w2, w3]
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int i3_0 = blockIdx.x * MT3, i2_0 = blockIdx.y * MT2, i1_0 = blockIdx.z * mt1;
+  const int i2 = i2_0 + ty, i3 = i3_0 + lane;
+  const bool active = i2 < g.n2 && i3 < g.n3;
+  const int64_t N = g.N, s1 = (int64_t)g.n2 * g.n3;
+  const int64_t col = active ? (int64_t)i2 * g.n3 + i3 : 0;
+  const float* w1 = w;
+  const float* w2 = w + N;
+  const float* w3 = w + 2 * N;
+  float q[9];                                                  // w1(i1 - 4 + k)
+#pragma unroll
+  for (int k = 0; k < 8; ++k) q[k] = active ? w1[wrap_any(i1_0 - 4 + k, g.n1) * s1 + col] : 0.f;
+  const int i1_end = min(i1_0 + mt1, g.n1);
+  const PlaneChunk ch = plane_chunk(g, i2_0, i3_0);
+  const bool vec = (g.n3 % 4 == 0) && ((reinterpret_cast<uintptr_t>(w) & 15) == 0);
+  stage_plane_async(w2, g, i1_0, i2_0, i3_0, ch, vec, sp[0][0]);
+  stage_plane_async(w3, g, i1_0, i2_0, i3_0, ch, vec, sp[0][1]);
+  cp_async_commit();
+  float hn = active ? w1[wrap_near(i1_0 + 4, g.n1) * s1 + col] : 0.f;
+  const int c = (ty + 4) * MP3 + lane + 4;                     // node in the staged plane
+  for (int i1 = i1_0; i1 < i1_end; ++i1) {
+    const int cur = (i1 - i1_0) & 1;
+    q[8] = hn;
+    if (i1 + 1 < i1_end) {
+      stage_plane_async(w2, g, i1 + 1, i2_0, i3_0, ch, vec, sp[cur ^ 1][0]);
+      stage_plane_async(w3, g, i1 + 1, i2_0, i3_0, ch, vec, sp[cur ^ 1][1]);
+      if (active) hn = w1[wrap_near(i1 + 5, g.n1) * s1 + col];
+    }
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();                                           // plane i1 staged by all
+    if (active) {
+      const float* p2 = sp[cur][0];
+      const float* p3 = sp[cur][1];
+      const float gx = fd8(q[0], q[1], q[2], q[3], q[5], q[6], q[7], q[8], g.inv_h1);
+      const float gy = fd8(p2[c - 4 * MP3], p2[c - 3 * MP3], p2[c - 2 * MP3], p2[c - MP3],
+                           p2[c + MP3], p2[c + 2 * MP3], p2[c + 3 * MP3], p2[c + 4 * MP3],
+                           g.inv_h2);
+      const float gz = fd8(p3[c - 4], p3[c - 3], p3[c - 2], p3[c - 1], p3[c + 1], p3[c + 2],
+                           p3[c + 3], p3[c + 4], g.inv_h3);
+      out[(int64_t)i1 * s1 + col] = gx + gy + gz;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+    __syncthreads();                                           // buffer cur consumed
+  }
 }
 
 // s^j = grad8(m^j) . vt for j = 0..nt (m^j = mhist + j N); s^0 is scaled by scale0.
@@ -1367,7 +1389,7 @@ void launch_affine(int64_t n, float a, const float* x, float b, float* out, cuda
 }
 void launch_div8(const Grid& g, const float* w, float* out, cudaStream_t st) {
   ProfileRange pr(K_DIV8, (double)g.N * 16, st);
-  k_div8<<<grid3(g), block3(), 0, st>>>(g, w, out);
+  k_div8_march<<<march_grid(g, MT1), dim3(32, MT2), 0, st>>>(g, w, out, MT1);
 }
 // History FD8 kernels: the marching version for nt in {1, 2, 4, 8}, the
 // per-node global-memory version for any other nt.

@@ -127,8 +127,10 @@ def test_far_node_count_matches_the_departure_points(claire):
             assert fwd > 0 and bwd > 0
 
 
-@pytest.mark.parametrize("shape", [RAGGED, CUBE])
+@pytest.mark.parametrize("shape", [RAGGED, CUBE, (40, 20, 34)])
 def test_fd8_gradient_and_divergence_match_oracle(claire, shape):
+    # (40, 20, 34): two x1 slabs of the divergence march (the second partial), a
+    # partial x2 tile and n3 % 4 != 0 (element-wise plane staging)
     u = synth.smooth_field(shape, 5, 3).astype(np.float32)
     w = synth.bandlimited_velocity(shape, 5, 2.0, 4).astype(np.float32)
     with claire.Context(shape) as ctx:
