@@ -318,7 +318,8 @@ claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
  *             whole CTA from the brick);
  *             2: the 64-load gather from a brick staged by the threads'
  *             16-byte cp.async copies.  All three give bitwise the same values
- *             (the FP16 form stages its bricks with cp.async for 0 and 2);
+ *             (the FP16 form's interior bricks land by TMA for 0 when
+ *             n3 % 8 == 0, else by cp.async);
  *  sl_t1      4, 8 or 16 nodes per thread along x1 (default 8);
  *  march_t1   8, 16, 32 or 64 planes per CTA of the FD8 history kernels (default 32).
  * EINVAL for any other value.  claire_get_tuning reads the current shapes (the

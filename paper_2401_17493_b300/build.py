@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libclaire.so")
 SOURCES = ["kernels.cu", "mixed.cu", "claire_api.cu", "noalloc.cu", "unet.cu", "precond.cu"]
-HEADERS = ["common.cuh", "internal.h", "sl_brick.cuh", "sl_window.cuh", "fd8_march.cuh",
+HEADERS = ["common.cuh", "internal.h", "sl_brick.cuh", "sl_tma.cuh", "sl_window.cuh", "fd8_march.cuh",
            "reduce.cuh",
            "device_setup.h", "tc_sm100.cuh"]
 

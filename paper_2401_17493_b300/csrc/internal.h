@@ -1,6 +1,7 @@
 // Internal declarations shared by the kernel launchers and the host solver.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cufft.h>
 #include <cuda_runtime.h>
@@ -60,8 +61,14 @@ bool tuned_sl_window();
 bool tuned_sl_tma();
 int tuned_march_t1();
 // Threads whose bounded wait for a TMA-staged SL brick ran out since the last
-// call (those CTAs gathered from global memory instead); reads and resets.
+// call (their outputs are left unwritten); reads and resets.  One counter for
+// the FP32 kernels (kernels.cu), one for the FP16 ones (mixed.cu).
 unsigned int take_brick_timeouts();
+unsigned int take_brick_timeouts_h();
+// TMA tensor map of ncomp stacked fields (FP32, or FP16 with half) whose box is
+// one SL brick of depth t1; false where TMA's alignment rules do not hold.
+bool encode_brick_map(CUtensorMap* m, const void* base, bool half, const Grid& g, int ncomp,
+                      int t1);
 
 struct ProfileRange {
   int kind;

@@ -28,6 +28,7 @@
 #include "sl_window.cuh"
 #include "fd8_march.cuh"
 #include "tc_sm100.cuh"
+#include "sl_tma.cuh"
 
 namespace claire {
 
@@ -41,63 +42,6 @@ namespace claire {
 static dim3 block3() { return dim3(32, 4, 2); }
 static dim3 grid3(const Grid& g) {
   return dim3((g.n3 + 31) / 32, (g.n2 + 3) / 4, (g.n1 + 1) / 2);
-}
-
-// ------------------------------------------------------ TMA brick staging
-
-// The SL bricks of k_sl and k_trace are staged by the tensor-memory accelerator
-// where the brick lies inside the grid: the source field is a 3D tensor map
-// (n3, n2, ncomp n1) and the whole brick is one box of BB3 x BB2 x (t1 + 6)
-// FP32 values (x3 x x2 x x1) at (i3_0 - 4, i2_0 - 3, c n1 + i1_0 - 3), written
-// densely into shared memory: rows of BB3 = 64 floats, the layout of
-// stage_brick, of which the gather reads the first BX3 = 40 (values beyond n3
-// in the padding are filled with zeros and never read).  One request per brick,
-// issued by one thread.  Bricks that wrap around the periodic grid (the tiles
-// at the ends of each axis, or grids narrower than a brick) are staged by the
-// threads' cp.async copies instead.  The load completes on an mbarrier.  The
-// wait is bounded: a thread whose wait runs out counts it in g_brick_timeouts
-// (read by claire_wait_status), waits once more (bounded) for the copy in
-// flight and leaves its outputs unwritten.
-constexpr uint32_t BRICK_WAIT = 1u << 20;       // try_wait calls of <= 1 us each
-
-__device__ unsigned int g_brick_timeouts = 0;
-
-// True when the tile's brick lies inside the grid on every axis: x3 range
-// [i3_0 - 4, i3_0 + 36), x2 range [i2_0 - 3, i2_0 + 11), x1 range
-// [i1_0 - 3, i1_0 + t1 + 3).
-__device__ __forceinline__ bool brick_tma_ok(const Grid& g, int i1_0, int i2_0, int i3_0,
-                                             int t1) {
-  return i3_0 - HB3_LO >= 0 && i3_0 - HB3_LO + BX3 <= g.n3 && i2_0 - HB_LO >= 0 &&
-         i2_0 + TB2 + HB_HI <= g.n2 && i1_0 - HB_LO >= 0 && i1_0 + t1 + HB_HI <= g.n1;
-}
-
-// mbarrier of the brick loads (one arrival per phase) set up by thread 0; the
-// caller's barrier publishes it before the first load.
-__device__ __forceinline__ void brick_mbar_init(uint64_t* mbar) {
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    mbar_init(mbar, 1);
-    fence_mbar_init();
-  }
-}
-
-// Thread 0 issues the TMA load of component c's brick into s; it completes on
-// the mbarrier's current phase.  The mbarrier must be set up and published, and
-// the shared brick no longer in use (a barrier since its last reads).
-__device__ __forceinline__ void issue_brick_tma(const CUtensorMap* map, int c, const Grid& g,
-                                                int i1_0, int i2_0, int i3_0,
-                                                float* __restrict__ s, int t1, uint64_t* mbar) {
-  if (threadIdx.x != 0 || threadIdx.y != 0) return;
-  fence_proxy_async_smem();                     // earlier generic accesses of the brick first
-  mbar_arrive_expect_tx(mbar, (uint32_t)brick_floats(t1) * (uint32_t)sizeof(float));
-  tma_load_3d(s, map, i3_0 - HB3_LO, i2_0 - HB_LO, c * g.n1 + i1_0 - HB_LO, mbar);
-}
-
-// Bounded wait for the brick loads of phase `parity`; false if it ran out (counted).
-__device__ __forceinline__ bool wait_brick_tma(uint64_t* mbar, uint32_t parity) {
-  if (mbar_wait(mbar, parity, BRICK_WAIT)) return true;
-  atomicAdd(&g_brick_timeouts, 1u);
-  (void)mbar_wait(mbar, parity, BRICK_WAIT);    // the copies in flight, again bounded
-  return false;
 }
 
 // ---------------------------------------------------------------- trace
@@ -1151,26 +1095,33 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map of ncomp consecutive FP32 fields of the grid starting at base, as
-// one n3 x n2 x (ncomp n1) tensor, box = one brick of depth t1 (BB3 x BB2 x
-// (t1 + 6)).  Returns false (the caller stages with cp.async) unless the fields
-// meet TMA's rules: base 16-byte aligned, the row pitch n3 * 4 bytes a multiple
-// of 16, and the grid at least one brick wide on every axis.
-static bool brick_map(const float* base, const Grid& g, int ncomp, int t1, CUtensorMap* m) {
+// Tensor map of ncomp consecutive fields of the grid starting at base (FP32, or
+// FP16 with half = true), as one n3 x n2 x (ncomp n1) tensor; box = one brick of
+// depth t1: BB3 x BB2 x (t1 + 6) FP32 values, or BRICK_H_BOX x BB2 x (t1 + 6)
+// halves.  Returns false (the caller stages with cp.async) unless the fields
+// meet TMA's rules: base 16-byte aligned, the row pitch a multiple of 16 bytes
+// (n3 % 4 == 0 for FP32, n3 % 8 == 0 for FP16), and the grid at least one brick
+// wide on every axis.
+bool encode_brick_map(CUtensorMap* m, const void* base, bool half, const Grid& g, int ncomp,
+                      int t1) {
   std::memset(m, 0, sizeof *m);
   const auto enc = tensor_map_encoder();
-  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || g.n3 % 4 != 0 ||
+  const int esize = half ? 2 : 4;
+  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (g.n3 * esize) % 16 != 0 ||
       g.n3 < BX3 || g.n2 < BB2 || g.n1 < t1 + HB_LO + HB_HI)
     return false;
   const cuuint64_t dims[3] = {(cuuint64_t)g.n3, (cuuint64_t)g.n2, (cuuint64_t)ncomp * g.n1};
-  const cuuint64_t strides[2] = {(cuuint64_t)g.n3 * sizeof(float),
-                                 (cuuint64_t)g.n2 * g.n3 * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)BB3, (cuuint32_t)BB2, (cuuint32_t)(t1 + HB_LO + HB_HI)};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.n3 * esize, (cuuint64_t)g.n2 * g.n3 * esize};
+  const cuuint32_t box[3] = {(cuuint32_t)(half ? BRICK_H_BOX : BB3), (cuuint32_t)BB2,
+                             (cuuint32_t)(t1 + HB_LO + HB_HI)};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return enc(m, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+static bool brick_map(const float* base, const Grid& g, int ncomp, int t1, CUtensorMap* m) {
+  return encode_brick_map(m, base, false, g, ncomp, t1);
 }
 
 // dynamic shared memory of k_sl / k_trace: the brick and its mbarrier

@@ -7,9 +7,10 @@
 // direction s.  Results are unscaled in FP32.
 //
 // SL bricks of FP16 fields are converted to FP32 once while they are staged in
-// shared memory, so the 64-tap gather is the FP32 one: the gather is
-// shared-memory / issue bound, and converting each staged value once is
-// cheaper than converting every tap.  (A layout holding each row twice as
+// shared memory (interior bricks land by one TMA box and are converted in place,
+// sl_tma.cuh; the others are copied with cp.async), so the 64-tap gather is the
+// FP32 one: the gather is shared-memory / issue bound, and converting each
+// staged value once is cheaper than converting every tap.  (A layout holding each row twice as
 // half2 pairs, halving the shared loads, was slower: every half still needs a
 // conversion instruction in the gather.)  The FD8 history march is the same
 // template as the FP32 form, instantiated for FP16 storage.
@@ -22,6 +23,7 @@
 #include "internal.h"
 #include "reduce.cuh"
 #include "sl_brick.cuh"
+#include "sl_tma.cuh"
 #include "sl_window.cuh"
 #include "fd8_march.cuh"
 
@@ -107,26 +109,43 @@ __device__ __forceinline__ float gather_global_h(const __half* __restrict__ u, c
 }
 
 // out = (scale ? scale(x) : sigma) u(x + d) + beta aux(x), u / aux / out in FP16.
+// With tma != 0 the interior bricks land by TMA from umap (FP16 boxes).
 __global__ void __launch_bounds__(BRICK_THREADS, 4) k_sl_h(Grid g, const __half* __restrict__ u,
                                                         const float* __restrict__ d,
                                                         const float* __restrict__ scale,
                                                         float sigma,
                                                         const __half* __restrict__ aux,
                                                         float beta, __half* __restrict__ out,
-                                                        int t1) {
-  extern __shared__ __align__(16) float smf[];
+                                                        int t1,
+                                                        const __grid_constant__ CUtensorMap umap,
+                                                        int tma) {
+  extern __shared__ __align__(128) float smf[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(smf) +
+                                               brick_floats(t1) * sizeof(float) + 128);
   const int i1_0 = blockIdx.z * t1, i2_0 = blockIdx.y * TB2, i3_0 = blockIdx.x * TB3;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i2 = i2_0 + ty, i3 = i3_0 + lane;
   const bool active = i2 < g.n2 && i3 < g.n3;
   const int64_t N = g.N, s1 = (int64_t)g.n2 * g.n3;
   const int64_t idx0 = active ? lin(g, i1_0, i2, i3) : 0;
+  const bool use_tma = tma && brick_tma_ok(g, i1_0, i2_0, i3_0, t1);
+  if (use_tma) {
+    brick_mbar_init(mbar);
+    __syncthreads();
+    issue_brick_tma_h(&umap, 0, g, i1_0, i2_0, i3_0, smf, t1, mbar);
+  }
   float dn[3];                                     // departure points, one node ahead
 #pragma unroll
   for (int a = 0; a < 3; ++a) dn[a] = active ? d[a * N + idx0] : 0.f;
-  stage_brick_h32(u, g, i1_0, i2_0, i3_0, smf, t1);
-  __syncthreads();
-  if (!active) return;
+  bool ok = true;
+  if (use_tma) {
+    ok = wait_brick_tma(mbar, 0u);
+    convert_brick_h(smf, t1);                      // ends with a barrier
+  } else {
+    stage_brick_h32(u, g, i1_0, i2_0, i3_0, smf, t1);
+    __syncthreads();
+  }
+  if (!active || !ok) return;
   const int kmax = min(t1, g.n1 - i1_0);
 #pragma unroll 2
   for (int k = 0; k < kmax; ++k) {
@@ -237,12 +256,21 @@ __global__ void __launch_bounds__(256) k_sqdiff_h(int64_t n, const __half* __res
 
 // ------------------------------------------------------------------ launchers
 
+unsigned int take_brick_timeouts_h() {
+  unsigned int n = 0;
+  const unsigned int zero = 0;
+  if (cudaMemcpyFromSymbol(&n, g_brick_timeouts, sizeof n) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_brick_timeouts, &zero, sizeof zero) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 void launch_sl_h(const Grid& g, const __half* u, const float* d, const float* scale,
                  float sigma, const __half* aux, float beta, __half* out, cudaStream_t st) {
   static std::once_flag once[kSetupDevices];
   once_per_device(once, [] {
     cudaFuncSetAttribute(k_sl_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         brick_floats(16) * (int)sizeof(float));
+                         (int)brick_h_smem_bytes(16));
     cudaFuncSetAttribute(k_slw_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          window_smem_bytes(16, 4, 1));
   });
@@ -252,9 +280,12 @@ void launch_sl_h(const Grid& g, const __half* u, const float* d, const float* sc
     k_slw_h<<<brick_grid(g, t1), dim3(32, TB2),
               window_smem_bytes(t1, 3 + (scale != nullptr), aux != nullptr), st>>>(
         g, u, d, scale, sigma, aux, beta, out, t1);
-  else
-    k_sl_h<<<brick_grid(g, t1), dim3(32, TB2), brick_floats(t1) * sizeof(float), st>>>(
-        g, u, d, scale, sigma, aux, beta, out, t1);
+  else {
+    CUtensorMap m;
+    const int tma = tuned_sl_tma() && encode_brick_map(&m, u, true, g, 1, t1);
+    k_sl_h<<<brick_grid(g, t1), dim3(32, TB2), brick_h_smem_bytes(t1), st>>>(
+        g, u, d, scale, sigma, aux, beta, out, t1, m, tma);
+  }
 }
 
 template <int MODE>

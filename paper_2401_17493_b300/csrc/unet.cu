@@ -1135,8 +1135,9 @@ __global__ void k_wait_selftest(uint32_t max_polls, int arrive) {
 }
 
 }  // namespace
-// threads whose bounded wait for a TMA-staged SL brick ran out (kernels.cu)
+// threads whose bounded wait for a TMA-staged SL brick ran out (kernels.cu, mixed.cu)
 unsigned int take_brick_timeouts();
+unsigned int take_brick_timeouts_h();
 }  // namespace claire
 
 using namespace claire;
@@ -1334,7 +1335,7 @@ claire_status claire_wait_status(int* timeouts) {
   if (cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof n) != cudaSuccess ||
       cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof zero) != cudaSuccess)
     return CLAIRE_ECUDA;
-  n += take_brick_timeouts();
+  n += take_brick_timeouts() + take_brick_timeouts_h();
   if (timeouts) *timeouts = (int)n;
   return n ? CLAIRE_ETIMEOUT : CLAIRE_OK;
 }

@@ -182,7 +182,7 @@ def test_autotuner_picks_valid_shapes_and_keeps_results(claire):
     assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
 
 
-GROUP_SHAPES = SHAPES + [(40, 36, 132)]        # the last one with TMA-staged interior bricks
+GROUP_SHAPES = SHAPES + [(40, 36, 136)]        # the last one with TMA-staged interior bricks
 
 
 def _group_contexts(C, precisions, **opts):
