@@ -49,7 +49,7 @@ INTERP_FD = ("trace", "sl_step", "adjoint_factor", "grad8", "div8", "sdot_hist",
 # of the capture: when the source differs, the figure is stale and
 # roofline.traffic is reported as null.
 NCU_TRAFFIC_PER_VOXEL = {
-    "sl_step": (23.27, "d8afd71044d82c5a2800fa4d096977c4c0e1e8acf28555cad4dba16a4df80da2")}
+    "sl_step": (23.27, "457bed694d4d863d84c9e3be41eedd6ee1e49b8f44b6984a8ace9529d0fff7b1")}
 # 64-tap gathers of a field per 256^3 registration of the headline solve (trace
 # components x directions + SL steps + adjoint factors), counted by the
 # library's launch profile in this bench's own arm ("field_gathers_per_registration"):
@@ -277,20 +277,19 @@ def run_batch(args, pairs):
 
 
 def sl_source_sha():
-    """SHA-256 of the SL step's source: in kernels.cu its TMA brick staging and
-    its tile function and kernel (each from its section comment to the next
-    section), sl_brick.cuh, common.cuh and tc_sm100.cuh."""
+    """SHA-256 of the SL step's source: in kernels.cu its tile function and
+    kernel (from the section comment to the next section), sl_tma.cuh (the TMA
+    brick staging), sl_brick.cuh, common.cuh and tc_sm100.cuh."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2401_17493_b300", "csrc")
     try:
         k = open(os.path.join(csrc, "kernels.cu")).read()
-        parts = [re.search(r"// -+ TMA brick staging\n.*?(?=// -+ trace\n)", k, flags=re.S),
-                 re.search(r"// MODE 0: out = .*?(?=// -+ grouped launches\n)", k, flags=re.S)]
-        if any(m is None for m in parts):
+        m = re.search(r"// MODE 0: out = .*?(?=// -+ grouped launches\n)", k, flags=re.S)
+        if m is None:
             return None
-        h = hashlib.sha256("".join(m.group(0) for m in parts).encode())
-        for f in ("sl_brick.cuh", "common.cuh", "tc_sm100.cuh"):
+        h = hashlib.sha256(m.group(0).encode())
+        for f in ("sl_tma.cuh", "sl_brick.cuh", "common.cuh", "tc_sm100.cuh"):
             h.update(open(os.path.join(csrc, f), "rb").read())
         return h.hexdigest()
     except OSError:
