@@ -464,15 +464,29 @@ def evaluate(model, pairs, n, beta, eps_opt=5e-2):
     return res
 
 
+def combined_chunks(npairs, batch):
+    """Index chunks of the combined arm: batch / 8 and batch / 2 pairs, then
+    `batch` pairs at a time (the last chunk takes the rest)."""
+    sizes, out, k = [max(1, batch // 8), max(1, batch // 2)], [], 0
+    while k < npairs:
+        m = min(sizes.pop(0) if sizes else batch, npairs - k)
+        out.append(list(range(k, k + m)))
+        k += m
+    return out
+
+
 def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
     """The plain method against the combined form on the same pairs.
 
     plain:    FP32 storage, zero initial guess, one pair after the other;
     combined: mixed precision (FP16 field storage), U-Net warm start with the
               J(v_pred) <= J(0) fallback inside the solver (options.warm_check), and
-              the pairs solved `batch` at a time by claire_solve_batch with
-              graph-captured PCG iterations; the prediction of the next batch runs
-              on a side stream while the current batch is solved.
+              the pairs solved up to `batch` at a time by claire_solve_batch with
+              graph-captured PCG iterations; the prediction of the next chunk runs
+              on a side stream while the current chunk is solved.  The chunks ramp
+              up (batch / 8, batch / 2, then batch pairs, `combined_chunks`), so
+              only the first, small chunk's prediction is not hidden behind solves:
+              a pair's prediction costs a fraction of its solve.
     Both arms stop at the same relative gradient with the same denominator
     |g(0)|_inf (from an FP32 evaluation at v = 0).  Context creation, one untimed
     set-up solve and g(0) are outside both timings; both arms reuse their contexts
@@ -509,9 +523,10 @@ def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
     # combined arm: a pool of `batch` contexts (workspace, cuFFT plans and captured
     # graphs set up once, outside the timing, by one untimed zero-initialised solve
     # of the first batch), then the timed pipeline over all pairs
-    chunks = [list(range(k, min(k + batch, len(pairs)))) for k in range(0, len(pairs), batch)]
+    chunks = combined_chunks(len(pairs), batch)
+    width = max(len(c) for c in chunks)
     pool = [C.Context((n, n, n), precision=1, graphs=1, warm_check=1, **opts)
-            for _ in chunks[0]]
+            for _ in range(width)]
 
     def load(idx):
         for i, cc in zip(idx, pool):
@@ -519,9 +534,15 @@ def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
             cc.set_options(gnorm0=gnorm0s[i])      # host-side option: graphs are kept
         return pool[:len(idx)]
 
-    C.solve_batch(load(chunks[0]), [zeros() for _ in chunks[0]])
+    C.solve_batch(load(list(range(width))), [zeros() for _ in range(width)])
     side = torch.cuda.Stream()
     main = torch.cuda.current_stream()
+    # diagnostic, untimed: the prediction of one full chunk on its own
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    _predict_batch(model, [pairs[i] for i in range(width)], n)
+    torch.cuda.synchronize()
+    t_pred_pair = (time.perf_counter() - tp) / width
 
     def predict(idx):
         side.wait_stream(main)
@@ -550,9 +571,10 @@ def evaluate_combined(model, pairs, n, beta, eps_opt=5e-2, batch=16):
     for c in pool:
         c.close()
     npairs = len(pairs)
-    summ = {"pairs": npairs, "batch": batch, "t_plain_per_pair": t_plain / npairs,
+    summ = {"pairs": npairs, "batch": batch, "chunks": [len(c) for c in chunks],
+            "t_plain_per_pair": t_plain / npairs,
             "t_combined_per_pair": t_comb / npairs, "speedup": t_plain / t_comb,
-            "fallbacks": fallbacks}
+            "t_prediction_per_pair": t_pred_pair, "fallbacks": fallbacks}
     for k in ("matvecs", "mismatch", "grad_rel"):
         for arm in ("plain", "combined"):
             summ[f"mean_{k}_{arm}"] = float(np.mean(res[f"{k}_{arm}"]))
