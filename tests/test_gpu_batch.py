@@ -233,3 +233,57 @@ def test_grouped_batch_continuation_and_reuse(claire):
         v2, st2 = ctx.solve_continuation(betas)
         assert np.array_equal(v.cpu().numpy(), v2.cpu().numpy())
         ctx.close()
+
+
+TUNINGS = [(0, 4, 16), (2, 16, 32), (0, 8, 64), (0, 16, 8), (2, 4, 32)]
+
+
+def test_grouped_batch_with_per_pair_tile_shapes(claire):
+    """Pairs with different gather variants, brick depths and march depths share
+    grouped launches (the launch's shared memory sized for the deepest brick, one
+    TMA box shape per pair): each pair still equals its own sequential solve with
+    the same shapes, bitwise."""
+    seq = []
+    for ctx, tune in zip(_group_contexts(claire, (0,) * 5), TUNINGS):
+        ctx.set_tuning(*tune)
+        v, st = ctx.solve()
+        seq.append((v.cpu().numpy(), st.matvecs))
+        ctx.close()
+    ctxs = _group_contexts(claire, (0,) * 5)
+    for ctx, tune in zip(ctxs, TUNINGS):
+        ctx.set_tuning(*tune)
+    for wait_us in (-1, 10):
+        vs, stats, _ = claire.solve_batch(ctxs, grouped=True, wait_us=wait_us)
+        for (vref, mv), v, st in zip(seq, vs, stats):
+            assert st.matvecs == mv
+            assert np.array_equal(v.cpu().numpy(), vref)
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("wait_us", [-1, 10])
+def test_grouped_batch_survives_a_failing_pair(claire, wait_us):
+    """A pair whose objective is not finite (NaN in its reference image) fails
+    after it has posted grouped launches; its thread leaves the group, the other
+    pairs finish with their sequential results and the call reports ENONFINITE."""
+    seq = []
+    for ctx in _group_contexts(claire, (0,) * 5):
+        v, _ = ctx.solve()
+        seq.append(v.cpu().numpy())
+        ctx.close()
+    ctxs = _group_contexts(claire, (0,) * 5)
+    bad = 2
+    shape = GROUP_SHAPES[bad]
+    m0, m1, _ = synth.blob_pair(shape, seed=300 + bad, kmax=3, max_disp_voxels=2.0)
+    m1 = m1.copy()
+    m1[1, 2, 3] = np.nan
+    ctxs[bad].set_images(dev(m0), dev(m1))
+    vs = [torch.zeros(c.vshape, device="cuda") for c in ctxs]
+    with pytest.raises(claire.ClaireError) as e:
+        claire.solve_batch(ctxs, vs, grouped=True, wait_us=wait_us)
+    assert e.value.status == claire.ENONFINITE
+    for i, (v, vref) in enumerate(zip(vs, seq)):
+        if i != bad:
+            assert np.array_equal(v.cpu().numpy(), vref)
+    for c in ctxs:
+        c.close()
