@@ -300,7 +300,7 @@ claire_status claire_solve_batch_grouped(claire_ctx** ctxs, int npairs, const do
                                          long long* group_ops);
 
 /* ---- autotuner -------------------------------------------------------------
- * Times the compiled tile shapes of the SL gather (both gather variants, brick
+ * Times the compiled tile shapes of the SL gather (the three gather variants, brick
  * depth along x1: 4, 8 or 16 nodes) and of the FD8 history kernels (8, 16, 32 or 64 planes per
  * CTA) on this context's grid and buffers and keeps the fastest for all later
  * calls on the context.  Evaluates J and g at the context's current v first if
@@ -321,7 +321,8 @@ claire_status claire_autotune(claire_ctx* ctx, int* sl_t1, int* march_t1);
  *             (the FP16 form's interior bricks land by TMA for 0 when
  *             n3 % 8 == 0, else by cp.async);
  *  sl_t1      4, 8 or 16 nodes per thread along x1 (default 8);
- *  march_t1   8, 16, 32 or 64 planes per CTA of the FD8 history kernels (default 32).
+ *  march_t1   8, 16, 32 or 64 planes per CTA of the FD8 history kernels (default 64
+ *             where that leaves at least four CTAs per multiprocessor, else 32).
  * EINVAL for any other value.  claire_get_tuning reads the current shapes (the
  * autotuner's choice after claire_autotune); NULL outputs are skipped. */
 claire_status claire_set_tuning(claire_ctx* ctx, int sl_gather, int sl_t1, int march_t1);

@@ -1400,6 +1400,7 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
   c->nt = nt;
   c->beta_v = beta_v;
   c->gamma = gamma;
+  c->tune.march_t1 = default_march_t1(g);
   const int64_t N = g.N;
   claire_status s = CLAIRE_OK;
   float** fields1[] = {&c->m0, &c->m1, &c->D, &c->cf, &c->pp0, &c->pp1};
@@ -1418,7 +1419,7 @@ claire_status claire_create(int nx, int ny, int nz, int nt, double beta_v, doubl
     // per-block partial sums of every fused reduction share one buffer
     int pb = c->red_blocks;
     pb = std::max(pb, spectral_blocks(g));
-    pb = std::max(pb, march_blocks(g));
+    pb = std::max(pb, march_blocks_max(g));        // any tunable depth
     pb = std::max(pb, vector_blocks(3 * N / 4));
     c->partial_blocks = pb;
     void* p = nullptr;

@@ -21,7 +21,7 @@
 
 namespace claire {
 
-constexpr int MT2 = 8, MT3 = 32, MT1 = 32;          // tile x2, x3; default planes per CTA
+constexpr int MT2 = 8, MT3 = 32, MT1 = 32;          // tile x2, x3; planes per CTA without a context
 constexpr int MP2 = MT2 + 8, MP3 = MT3 + 8;         // staged plane with the FD8 halo
 constexpr int MPLANE = MP2 * MP3;                   // 640 floats
 

@@ -102,6 +102,8 @@ void launch_accum_hist(const Grid& g, const float* lhist, const float* mhist, in
                        const float* base, float base_coef, float* out, cudaStream_t st,
                        const float* dotv = nullptr, double* partial = nullptr);
 int march_blocks(const Grid& g);
+int march_blocks_max(const Grid& g);        // blocks at the shallowest tunable depth
+int default_march_t1(const Grid& g);        // default planes per CTA for this grid
 bool march_supported(int nt);
 // partial (optional): per-block shares of <in, out>; means (optional): the
 // three component means of the input field.  spectral_blocks() blocks.

@@ -1379,6 +1379,19 @@ int march_blocks(const Grid& g) {
   const dim3 m = march_grid(g, tuned_march_t1());
   return (int)(m.x * m.y * m.z);
 }
+int march_blocks_max(const Grid& g) {                 // at the shallowest depth, 8 planes
+  const dim3 m = march_grid(g, 8);
+  return (int)(m.x * m.y * m.z);
+}
+// 64 planes per CTA (fewer queue refills: each CTA re-reads 8 planes of every
+// history field to fill its queues) where that still leaves at least four CTAs
+// per multiprocessor, else 32.
+int default_march_t1(const Grid& g) {
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 148;
+  const dim3 m = march_grid(g, 64);
+  return (int64_t)m.x * m.y * m.z >= 4LL * sms ? 64 : 32;
+}
 bool march_supported(int nt) { return nt == 1 || nt == 2 || nt == 4 || nt == 8; }
 
 void launch_sdot_hist(const Grid& g, const float* mhist, int nt, const float* vt, float scale0,

@@ -32,6 +32,8 @@ def main():
                          "brick, 1 register window, 2 64 loads from a cp.async-staged brick)")
     ap.add_argument("--sl-t1", type=int, default=None, choices=[4, 8, 16],
                     help="SL brick depth along x1")
+    ap.add_argument("--march-t1", type=int, default=None, choices=[8, 16, 32, 64],
+                    help="planes per CTA of the FD8 history kernels")
     args = ap.parse_args()
     import torch
     from paper_2401_17493_b300 import build, claire, synth
@@ -43,10 +45,11 @@ def main():
     u = torch.rand(shape, device="cuda", generator=gen)
     v = torch.from_numpy(synth.bandlimited_velocity(shape, 8, 4.0, 3).astype(np.float32)).cuda()
     ctx = claire.Context(shape, nt=4, precision=args.precision)
-    if args.sl_gather is not None or args.sl_t1 is not None:
+    if args.sl_gather is not None or args.sl_t1 is not None or args.march_t1 is not None:
         w0, t0, m0 = ctx.tuning()
         ctx.set_tuning(w0 if args.sl_gather is None else args.sl_gather,
-                       t0 if args.sl_t1 is None else args.sl_t1, m0)
+                       t0 if args.sl_t1 is None else args.sl_t1,
+                       m0 if args.march_t1 is None else args.march_t1)
     ctx.set_images(u, u)
     d, _ = ctx.trace(v)
     out1 = torch.empty(shape, device="cuda")
