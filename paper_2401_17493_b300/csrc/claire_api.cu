@@ -1885,13 +1885,15 @@ namespace claire {
 // round's leader: it waits until every live worker has posted or until
 // wait_us microseconds have passed since its own post (wait_us < 0: no time
 // limit), whichever comes first, and then launches everything posted so far,
-// one persistent grouped launch per kind, on the group's stream.  Workers that post later go into the next round, so a
-// pair busy with other work (cuFFT, a host synchronisation) does not hold the
-// others back for long.  Ordering: a poster records an event on its pair's
-// stream and makes the group's stream wait for it before posting; the leader
-// records `done` behind the grouped launches and makes each flushed pair's
-// stream wait for it while it holds the lock, so no event is re-recorded before
-// its waits are enqueued.
+// one persistent grouped launch per kind, on the group's stream.  Workers that
+// post later go into the next round, so a pair busy with other work (cuFFT, a
+// host synchronisation) does not hold the others back for long.  Ordering: a
+// poster records an event on its pair's stream and makes the group's stream
+// wait for it before posting (a wait that lands between the launches of a
+// concurrent flush only delays them); the flushing thread records `done`
+// behind the grouped launches and makes each flushed pair's stream wait for it
+// while it holds the lock, so no event is re-recorded before its waits are
+// enqueued.
 class LaunchGroup {
  public:
   LaunchGroup(int live, cudaStream_t gst, cudaEvent_t done, int wait_us)
